@@ -1,0 +1,205 @@
+"""CPU oracle for the inter-visibility matrix, table and image tree.
+
+TEST INFRASTRUCTURE ONLY: the test suite, the smoke check and the CPU
+baseline leg of the benchmark call it; the CUDA library never does.  The
+arithmetic lives in ``ivm_oracle.c`` (plain C, exact __int128, brute force
+with no acceleration structure); this module compiles it with gcc and
+marshals numpy arrays.  Work is spread over threads by row / snapshot
+range; ctypes releases the GIL during each foreign call.
+
+The definition it computes, with the paper sections it follows, is in the
+header comment of ``ivm_oracle.c``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from concurrent.futures import ThreadPoolExecutor
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "ivm_oracle.c")
+_OUT = os.path.join(_HERE, "_build", "libivm_oracle.so")
+_lib = None
+
+_i32p = ctypes.POINTER(ctypes.c_int32)
+_i64p = ctypes.POINTER(ctypes.c_int64)
+_u32p = ctypes.POINTER(ctypes.c_uint32)
+_u64p = ctypes.POINTER(ctypes.c_uint64)
+_u8p = ctypes.POINTER(ctypes.c_uint8)
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (no vendor flags, same on x86 and Arm)."""
+    if force or not os.path.exists(_OUT) or os.path.getmtime(_OUT) < os.path.getmtime(_SRC):
+        os.makedirs(os.path.dirname(_OUT), exist_ok=True)
+        tmp = _OUT + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-Wall",
+                               "-Wextra", "-Wno-unused-parameter", "-o", tmp, _SRC])
+        os.replace(tmp, _OUT)
+    return _OUT
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        L = ctypes.CDLL(build())
+        L.oracle_seg_hits_tri.argtypes = [_i64p] * 5
+        L.oracle_seg_hits_tri.restype = ctypes.c_int
+        L.oracle_blocked.argtypes = [_i32p, ctypes.c_int32, ctypes.c_int32, _i64p, _i64p]
+        L.oracle_blocked.restype = ctypes.c_int
+        L.oracle_matrix_rows.argtypes = [_i32p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                         ctypes.c_int32, _u32p]
+        L.oracle_matrix_rows.restype = None
+        L.oracle_table.argtypes = [_i32p, ctypes.c_int32, ctypes.c_int32, _i32p, _i32p,
+                                   ctypes.c_int64, ctypes.c_int64, _u32p, _u8p]
+        L.oracle_table.restype = None
+        L.oracle_tree.argtypes = [_u32p, _u32p, _u8p, ctypes.c_int32, ctypes.c_int64,
+                                  ctypes.c_int64, ctypes.c_int32, _u64p, _i32p, ctypes.c_int64,
+                                  _i64p]
+        L.oracle_tree.restype = None
+        L.oracle_traditional.argtypes = [_i32p, ctypes.c_int32, ctypes.c_int32, _i32p, _i32p,
+                                         ctypes.c_int64, ctypes.c_int64, ctypes.c_int32, _u64p]
+        L.oracle_traditional.restype = None
+        L.oracle_pair_free_count.argtypes = [_i32p, ctypes.c_int32, ctypes.c_int32,
+                                             ctypes.c_int32, ctypes.c_int32]
+        L.oracle_pair_free_count.restype = ctypes.c_int64
+        L.oracle_splitmix64.argtypes = [ctypes.c_uint64]
+        L.oracle_splitmix64.restype = ctypes.c_uint64
+        L.oracle_fp_weight.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]
+        L.oracle_fp_weight.restype = ctypes.c_uint64
+        _lib = L
+    return _lib
+
+
+def _p(a, t):
+    return a.ctypes.data_as(t)
+
+
+def words(n: int) -> int:
+    return (n + 31) // 32
+
+
+def _threads(threads):
+    return threads or os.cpu_count() or 1
+
+
+def _facets(facets):
+    return np.ascontiguousarray(facets, dtype=np.int32).reshape(-1, 10)
+
+
+def seg_hits_tri(P, Q, A, B, C) -> bool:
+    arr = [np.ascontiguousarray(x, dtype=np.int64) for x in (P, Q, A, B, C)]
+    return bool(lib().oracle_seg_hits_tri(*[_p(x, _i64p) for x in arr]))
+
+
+def blocked(facets, s, P, Q) -> bool:
+    F = _facets(facets)
+    P = np.ascontiguousarray(P, dtype=np.int64)
+    Q = np.ascontiguousarray(Q, dtype=np.int64)
+    return bool(lib().oracle_blocked(_p(F, _i32p), F.shape[0], s, _p(P, _i64p), _p(Q, _i64p)))
+
+
+def pair_free_count(facets, s, i, j) -> int:
+    F = _facets(facets)
+    return int(lib().oracle_pair_free_count(_p(F, _i32p), F.shape[0], s, i, j))
+
+
+def matrix(facets, s, rows=None, threads=None) -> np.ndarray:
+    """Matrix rows (all rows by default): uint32 [len(rows)][W]."""
+    F = _facets(facets)
+    n = F.shape[0]
+    rows = np.arange(n) if rows is None else np.asarray(rows, dtype=np.int64)
+    out = np.zeros((len(rows), words(n)), dtype=np.uint32)
+    L = lib()
+
+    def one(k):
+        r = int(rows[k])
+        L.oracle_matrix_rows(_p(F, _i32p), n, s, r, r + 1, _p(out[k], _u32p))
+
+    with ThreadPoolExecutor(_threads(threads)) as ex:
+        list(ex.map(one, range(len(rows))))
+    return out
+
+
+def table(facets, s, tx, rx, snaps=None, threads=None):
+    """Table rows for the given snapshots: (uint32 [n][2][W], uint8 [n])."""
+    F = _facets(facets)
+    n = F.shape[0]
+    tx = np.ascontiguousarray(tx, dtype=np.int32).reshape(-1, 3)
+    rx = np.ascontiguousarray(rx, dtype=np.int32).reshape(-1, 3)
+    snaps = np.arange(tx.shape[0]) if snaps is None else np.asarray(snaps, dtype=np.int64)
+    tab = np.zeros((len(snaps), 2, words(n)), dtype=np.uint32)
+    los = np.zeros(len(snaps), dtype=np.uint8)
+    L = lib()
+
+    def one(k):
+        t = int(snaps[k])
+        L.oracle_table(_p(F, _i32p), n, s, _p(tx, _i32p), _p(rx, _i32p), t, t + 1,
+                       _p(tab[k], _u32p), _p(los[k:k + 1], _u8p))
+
+    with ThreadPoolExecutor(_threads(threads)) as ex:
+        list(ex.map(one, range(len(snaps))))
+    return tab, los
+
+
+def tree(M, tab, los, n, K, paths=False, cap=0, threads=None):
+    """Summaries uint64 [S][K+1][3]; with paths=True also the path records
+    int32 [n_paths][K+2] = (t, k, f1..fK, -1 padded) in DFS order."""
+    M = np.ascontiguousarray(M, dtype=np.uint32)
+    tab = np.ascontiguousarray(tab, dtype=np.uint32)
+    los = np.ascontiguousarray(los, dtype=np.uint8)
+    S = tab.shape[0]
+    summ = np.zeros((S, K + 1, 3), dtype=np.uint64)
+    L = lib()
+    if paths:
+        cnt = np.zeros(1, dtype=np.int64)
+        L.oracle_tree(_p(M, _u32p), _p(tab, _u32p), _p(los, _u8p), n, 0, S, K,
+                      _p(summ, _u64p), None, 0, _p(cnt, _i64p))
+        total = int(cnt[0])
+        recs = np.zeros((max(total, 1), K + 2), dtype=np.int32)
+        cnt[0] = 0
+        L.oracle_tree(_p(M, _u32p), _p(tab, _u32p), _p(los, _u8p), n, 0, S, K,
+                      _p(summ, _u64p), _p(recs, _i32p), total, _p(cnt, _i64p))
+        return summ, recs[:total]
+
+    chunk = max(1, S // (4 * _threads(threads)))
+
+    def one(t0):
+        t1 = min(S, t0 + chunk)
+        L.oracle_tree(_p(M, _u32p), _p(tab, _u32p), _p(los, _u8p), n, t0, t1, K,
+                      _p(summ[t0:t1], _u64p), None, 0, None)
+
+    with ThreadPoolExecutor(_threads(threads)) as ex:
+        list(ex.map(one, range(0, S, chunk)))
+    return summ
+
+
+def traditional(facets, s, tx, rx, K, snaps=None, threads=None):
+    """Per-snapshot recomputation with no cached matrix: uint64 [n][K+1][3]."""
+    F = _facets(facets)
+    n = F.shape[0]
+    tx = np.ascontiguousarray(tx, dtype=np.int32).reshape(-1, 3)
+    rx = np.ascontiguousarray(rx, dtype=np.int32).reshape(-1, 3)
+    snaps = np.arange(tx.shape[0]) if snaps is None else np.asarray(snaps, dtype=np.int64)
+    summ = np.zeros((len(snaps), K + 1, 3), dtype=np.uint64)
+    L = lib()
+
+    def one(k):
+        t = int(snaps[k])
+        L.oracle_traditional(_p(F, _i32p), n, s, _p(tx, _i32p), _p(rx, _i32p), t, t + 1, K,
+                             _p(summ[k], _u64p))
+
+    with ThreadPoolExecutor(_threads(threads)) as ex:
+        list(ex.map(one, range(len(snaps))))
+    return summ
+
+
+def splitmix64(x: int) -> int:
+    return int(lib().oracle_splitmix64(x))
+
+
+def fp_weight(c: int, m: int, f: int) -> int:
+    return int(lib().oracle_fp_weight(c, m, f))

@@ -1,0 +1,454 @@
+/*
+ * ivm_oracle.c -- CPU oracle for the inter-visibility matrix, the per-snapshot
+ * inter-visibility table and the image-tree path sets.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the slow, plain, obviously-correct
+ * definition that the CUDA library is compared against.  Only the test suite,
+ * the smoke check and the CPU-baseline leg of the benchmark load it.  It shares
+ * no code, header, table or helper with the CUDA library, and the CUDA library
+ * never calls it.
+ *
+ * Everything is brute force: every sample pair against every triangle of the
+ * scene, no acceleration structure, exact __int128 arithmetic throughout.
+ *
+ * The definition (paper sections in brackets):
+ *
+ *  1. Scale.  Coordinates (integer cm) are multiplied by 2s, s = samples per
+ *     side, so that every sample point is an integer.  Facet f is the
+ *     parallelogram {o + a u + b v : a, b in [0,1]}; its outward normal is
+ *     n_f = u x v.  It is split into triangles A = (o, o+u, o+u+v) and
+ *     B = (o, o+u+v, o+v) [the scene's faces are triangulated, Sec. IV-B].
+ *     Samples are the s*s cell centres p_ab = 2s o + (2a+1) u + (2b+1) v.
+ *  2. Facing.  front(x, f) <=> n_f . (x - 2s o_f) > 0.  Only the outward
+ *     side of a face can be visible, and an angle of 180 degrees or more
+ *     counts as not visible [Sec. II-B, Eq. (2)], hence the strict sign.
+ *  3. Occlusion ("intersection judgment") [Abstract; Sec. I contributions;
+ *     Sec. II-B: the reference face reaches the aim face with no other
+ *     obstacle; Sec. III-A: blockage by nearby buildings].
+ *     blocked(P, Q) <=> some triangle of the scene meets the OPEN segment
+ *     {P + l (Q - P) : 0 < l < 1}; triangles are CLOSED (touching blocks).
+ *  4. Matrix [Sec. II].  M_ij = [i != j] and there are samples p_a of i and
+ *     q_b of j with front(q_b, i), front(p_a, j) and not blocked(p_a, q_b).
+ *     Partial visibility counts as visible [Sec. III-A, Fig. 4].  The Tx is
+ *     not involved [Sec. II-B: Tx-to-reference-face visibility is assumed].
+ *  5. Table [Sec. III-B/C, Table II].  vis_X[t][j] = front(X_t, j) and some
+ *     sample q_b of j has not blocked(X_t, q_b), for X in {Tx, Rx};
+ *     los[t] = not blocked(Tx_t, Rx_t) (1 when Tx_t = Rx_t).
+ *  6. Image tree [Sec. II intro; Sec. III-B, Table II rows are (parent =
+ *     transmitter, reference face, aim face); Sec. III-C].  Order-k paths are
+ *     (f1..fk) with vis_Tx[f1], M[f_m][f_m+1] for every hop, vis_Rx[fk].
+ *     Order 0 is the direct path (los).  Paths are enumerated by depth-first
+ *     search; the summary per (snapshot, order) is the path count and two
+ *     fingerprints sum over paths of prod_m h_c(m, f_m) mod 2^64 with
+ *     h_c(m, f) = splitmix64(seed_c ^ (m << 32) ^ f) | 1.
+ *  7. Traditional per-snapshot method [Sec. IV-B, brute-force image tree per
+ *     location]: the same path sets with every hop's visibility recomputed
+ *     from geometry at every snapshot, no cached matrix.
+ *
+ * Bit layout of rows: bit j of a row is word j >> 5, bit j & 31 (LSB first);
+ * W = ceil(N / 32) words per row; padding bits are 0.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+typedef __int128 i128;
+
+/* ---------------------------------------------------------------- vectors */
+
+typedef struct { i128 x, y, z; } V;
+
+static V mk(i128 x, i128 y, i128 z) { V r = {x, y, z}; return r; }
+static V sub(V a, V b) { return mk(a.x - b.x, a.y - b.y, a.z - b.z); }
+static V add(V a, V b) { return mk(a.x + b.x, a.y + b.y, a.z + b.z); }
+static V scl(i128 k, V a) { return mk(k * a.x, k * a.y, k * a.z); }
+static i128 dot(V a, V b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+static V cross(V a, V b)
+{
+    return mk(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+static int sgn(i128 v) { return (v > 0) - (v < 0); }
+static int veq(V a, V b) { return a.x == b.x && a.y == b.y && a.z == b.z; }
+
+/* orient3d(a, b, c, d) = det[b - a, c - a, d - a] */
+static i128 orient3d(V a, V b, V c, V d)
+{
+    return dot(sub(b, a), cross(sub(c, a), sub(d, a)));
+}
+
+/* ---------------------------------------------------------------- facets */
+
+typedef struct {
+    V o, u, v;        /* unscaled, cm */
+    V n;              /* u x v, outward */
+    V O;              /* 2s o, scaled */
+    V tri[2][3];      /* triangles A and B, scaled */
+} Facet;
+
+static Facet facet_of(const int32_t *r, int s)
+{
+    Facet f;
+    i128 k = 2 * (i128)s;
+    f.o = mk(r[0], r[1], r[2]);
+    f.u = mk(r[3], r[4], r[5]);
+    f.v = mk(r[6], r[7], r[8]);
+    f.n = cross(f.u, f.v);
+    f.O = scl(k, f.o);
+    V a = f.O, b = scl(k, add(f.o, f.u)), c = scl(k, add(add(f.o, f.u), f.v)),
+      d = scl(k, add(f.o, f.v));
+    f.tri[0][0] = a; f.tri[0][1] = b; f.tri[0][2] = c;   /* A = (o, o+u, o+u+v) */
+    f.tri[1][0] = a; f.tri[1][1] = c; f.tri[1][2] = d;   /* B = (o, o+u+v, o+v) */
+    return f;
+}
+
+static Facet *load_facets(const int32_t *facets, int32_t n, int s)
+{
+    Facet *F = (Facet *)malloc(sizeof(Facet) * (size_t)(n > 0 ? n : 1));
+    for (int32_t i = 0; i < n; i++) F[i] = facet_of(facets + 10 * (size_t)i, s);
+    return F;
+}
+
+static V sample(const Facet *f, int s, int a, int b)
+{
+    return add(f->O, add(scl(2 * a + 1, f->u), scl(2 * b + 1, f->v)));
+}
+
+/* step 2: strict facing */
+static int front(V x, const Facet *f) { return dot(f->n, sub(x, f->O)) > 0; }
+
+/* ------------------------------------------------ step 3: segment vs triangle */
+
+/* a/b < c/d for b, d > 0 */
+static int frac_lt(i128 a, i128 b, i128 c, i128 d) { return a * d < c * b; }
+static int frac_le(i128 a, i128 b, i128 c, i128 d) { return a * d <= c * b; }
+
+/* Coplanar case: P, Q and the triangle lie in one plane.  The set of
+ * l in [0,1] with P + l d inside the closed triangle is an interval [lo, hi];
+ * it is found by clipping against the three edge half-planes in the
+ * projection that drops the normal's dominant axis.  The open segment meets
+ * the triangle iff lo <= hi, lo < 1 and hi > 0. */
+static int coplanar_hit(V P, V Q, V A, V B, V C)
+{
+    V n = cross(sub(B, A), sub(C, A));
+    i128 ax = n.x < 0 ? -n.x : n.x, ay = n.y < 0 ? -n.y : n.y, az = n.z < 0 ? -n.z : n.z;
+    int drop = (ax >= ay && ax >= az) ? 0 : (ay >= az ? 1 : 2);
+    i128 p[3][2], pp[2], dd[2];
+    V T[3] = {A, B, C};
+    V d = sub(Q, P);
+    for (int i = 0; i < 3; i++) {
+        i128 c3[3] = {T[i].x, T[i].y, T[i].z};
+        int m = 0;
+        for (int k = 0; k < 3; k++) if (k != drop) p[i][m++] = c3[k];
+    }
+    {
+        i128 c3[3] = {P.x, P.y, P.z}, e3[3] = {d.x, d.y, d.z};
+        int m = 0;
+        for (int k = 0; k < 3; k++) if (k != drop) { pp[m] = c3[k]; dd[m] = e3[k]; m++; }
+    }
+    /* orientation of the projected triangle */
+    i128 area = (p[1][0] - p[0][0]) * (p[2][1] - p[0][1]) - (p[1][1] - p[0][1]) * (p[2][0] - p[0][0]);
+    int sig = sgn(area);
+    if (sig == 0) return 0;   /* degenerate triangle: never produced by valid facets */
+    i128 lo_n = 0, lo_d = 1, hi_n = 1, hi_d = 1;
+    for (int e = 0; e < 3; e++) {
+        const i128 *a = p[e], *b = p[(e + 1) % 3];
+        i128 ex = b[0] - a[0], ey = b[1] - a[1];
+        /* inside <=> sig * cross2(edge, X - a) >= 0 with X = P + l d */
+        i128 alpha = sig * (ex * (pp[1] - a[1]) - ey * (pp[0] - a[0]));
+        i128 beta = sig * (ex * dd[1] - ey * dd[0]);
+        if (beta > 0) {            /* l >= -alpha / beta */
+            if (frac_lt(lo_n, lo_d, -alpha, beta)) { lo_n = -alpha; lo_d = beta; }
+        } else if (beta < 0) {     /* l <= alpha / (-beta) */
+            if (frac_lt(alpha, -beta, hi_n, hi_d)) { hi_n = alpha; hi_d = -beta; }
+        } else if (alpha < 0) {
+            return 0;
+        }
+    }
+    return frac_le(lo_n, lo_d, hi_n, hi_d) && frac_lt(lo_n, lo_d, 1, 1) && frac_lt(0, 1, hi_n, hi_d);
+}
+
+/* Open segment PQ against closed triangle ABC. */
+static int seg_hits_tri(V P, V Q, V A, V B, V C)
+{
+    if (veq(P, Q)) return 0;                 /* empty open segment */
+    int oP = sgn(orient3d(A, B, C, P));
+    int oQ = sgn(orient3d(A, B, C, Q));
+    if (oP != 0 && oP == oQ) return 0;       /* same strict side */
+    if ((oP == 0) != (oQ == 0)) return 0;    /* touches the plane only at an endpoint */
+    if (oP != 0) {                           /* strictly opposite sides */
+        int e1 = sgn(orient3d(P, Q, A, B));
+        int e2 = sgn(orient3d(P, Q, B, C));
+        int e3 = sgn(orient3d(P, Q, C, A));
+        return (e1 >= 0 && e2 >= 0 && e3 >= 0) || (e1 <= 0 && e2 <= 0 && e3 <= 0);
+    }
+    return coplanar_hit(P, Q, A, B, C);
+}
+
+static int blocked(const Facet *F, int32_t n, V P, V Q)
+{
+    for (int32_t k = 0; k < n; k++)
+        for (int t = 0; t < 2; t++)
+            if (seg_hits_tri(P, Q, F[k].tri[t][0], F[k].tri[t][1], F[k].tri[t][2])) return 1;
+    return 0;
+}
+
+/* step 4, one ordered pair */
+static int pair_visible(const Facet *F, int32_t n, int s, int32_t i, int32_t j)
+{
+    if (i == j) return 0;
+    for (int a0 = 0; a0 < s; a0++)
+        for (int a1 = 0; a1 < s; a1++) {
+            V p = sample(&F[i], s, a0, a1);
+            if (!front(p, &F[j])) continue;
+            for (int b0 = 0; b0 < s; b0++)
+                for (int b1 = 0; b1 < s; b1++) {
+                    V q = sample(&F[j], s, b0, b1);
+                    if (!front(q, &F[i])) continue;
+                    if (!blocked(F, n, p, q)) return 1;
+                }
+        }
+    return 0;
+}
+
+/* step 5, one (point, facet) entry */
+static int point_sees(const Facet *F, int32_t n, int s, V X, int32_t j)
+{
+    if (!front(X, &F[j])) return 0;
+    for (int b0 = 0; b0 < s; b0++)
+        for (int b1 = 0; b1 < s; b1++)
+            if (!blocked(F, n, X, sample(&F[j], s, b0, b1))) return 1;
+    return 0;
+}
+
+static V point_of(const int32_t *p, int s)
+{
+    return scl(2 * (i128)s, mk(p[0], p[1], p[2]));
+}
+
+/* ------------------------------------------------------------- public API */
+
+#define OR_EXPORT __attribute__((visibility("default")))
+
+OR_EXPORT int32_t oracle_words(int32_t n) { return (n + 31) / 32; }
+
+/* Predicate on scaled integer points (for the predicate tests). */
+OR_EXPORT int oracle_seg_hits_tri(const int64_t *P, const int64_t *Q, const int64_t *A,
+                                  const int64_t *B, const int64_t *C)
+{
+    return seg_hits_tri(mk(P[0], P[1], P[2]), mk(Q[0], Q[1], Q[2]), mk(A[0], A[1], A[2]),
+                        mk(B[0], B[1], B[2]), mk(C[0], C[1], C[2]));
+}
+
+/* blocked(P, Q) against a whole scene; P, Q are scaled (x 2s) points. */
+OR_EXPORT int oracle_blocked(const int32_t *facets, int32_t n, int32_t s, const int64_t *P,
+                             const int64_t *Q)
+{
+    Facet *F = load_facets(facets, n, s);
+    int r = blocked(F, n, mk(P[0], P[1], P[2]), mk(Q[0], Q[1], Q[2]));
+    free(F);
+    return r;
+}
+
+/* Number of sample pairs (p_a on i, q_b on j) that satisfy the three
+ * conditions of step 4 (for the hand-counted partial-blocker scene). */
+OR_EXPORT int64_t oracle_pair_free_count(const int32_t *facets, int32_t n, int32_t s, int32_t i,
+                                         int32_t j)
+{
+    Facet *F = load_facets(facets, n, s);
+    int64_t cnt = 0;
+    for (int a0 = 0; a0 < s; a0++)
+        for (int a1 = 0; a1 < s; a1++) {
+            V p = sample(&F[i], s, a0, a1);
+            if (!front(p, &F[j])) continue;
+            for (int b0 = 0; b0 < s; b0++)
+                for (int b1 = 0; b1 < s; b1++) {
+                    V q = sample(&F[j], s, b0, b1);
+                    if (front(q, &F[i]) && !blocked(F, n, p, q)) cnt++;
+                }
+        }
+    free(F);
+    return cnt;
+}
+
+/* Rows [row0, row1) of the matrix: out is (row1 - row0) x W words. */
+OR_EXPORT void oracle_matrix_rows(const int32_t *facets, int32_t n, int32_t s, int32_t row0,
+                                  int32_t row1, uint32_t *out)
+{
+    int32_t W = oracle_words(n);
+    Facet *F = load_facets(facets, n, s);
+    memset(out, 0, sizeof(uint32_t) * (size_t)W * (size_t)(row1 - row0));
+    for (int32_t i = row0; i < row1; i++)
+        for (int32_t j = 0; j < n; j++)
+            if (pair_visible(F, n, s, i, j))
+                out[(size_t)(i - row0) * W + (j >> 5)] |= 1u << (j & 31);
+    free(F);
+}
+
+/* Snapshots [t0, t1) of the table: table is (t1 - t0) x 2 x W (Tx row, Rx
+ * row), los is (t1 - t0) bytes.  tx, rx are the full [S][3] arrays (cm). */
+OR_EXPORT void oracle_table(const int32_t *facets, int32_t n, int32_t s, const int32_t *tx,
+                            const int32_t *rx, int64_t t0, int64_t t1, uint32_t *table,
+                            uint8_t *los)
+{
+    int32_t W = oracle_words(n);
+    Facet *F = load_facets(facets, n, s);
+    memset(table, 0, sizeof(uint32_t) * (size_t)W * 2 * (size_t)(t1 - t0));
+    for (int64_t t = t0; t < t1; t++) {
+        V X[2] = {point_of(tx + 3 * t, s), point_of(rx + 3 * t, s)};
+        uint32_t *row = table + (size_t)(t - t0) * 2 * W;
+        for (int side = 0; side < 2; side++)
+            for (int32_t j = 0; j < n; j++)
+                if (point_sees(F, n, s, X[side], j))
+                    row[side * W + (j >> 5)] |= 1u << (j & 31);
+        los[t - t0] = (uint8_t)!blocked(F, n, X[0], X[1]);
+    }
+    free(F);
+}
+
+/* ------------------------------------------------------- step 6: image tree */
+
+static uint64_t splitmix64(uint64_t x)
+{
+    uint64_t z = x + 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+static const uint64_t FP_SEED[2] = {0x243F6A8885A308D3ull, 0x13198A2E03707344ull};
+
+OR_EXPORT uint64_t oracle_splitmix64(uint64_t x) { return splitmix64(x); }
+
+OR_EXPORT uint64_t oracle_fp_weight(int32_t c, int32_t m, int32_t f)
+{
+    return splitmix64(FP_SEED[c] ^ ((uint64_t)(uint32_t)m << 32) ^ (uint64_t)(uint32_t)f) | 1ull;
+}
+
+static int bit(const uint32_t *row, int32_t j) { return (row[j >> 5] >> (j & 31)) & 1u; }
+
+typedef struct {
+    const uint32_t *M, *tx_row, *rx_row;
+    int32_t n, W, k, t;
+    int32_t path[32];
+    uint64_t count, fp[2];
+    int32_t *paths;        /* nullable */
+    int64_t cap, *n_paths;
+    int32_t K;
+    /* traditional mode: recompute hops from geometry */
+    const Facet *F;
+    int s;
+} Dfs;
+
+static void emit(Dfs *d)
+{
+    uint64_t w0 = 1, w1 = 1;
+    for (int m = 1; m <= d->k; m++) {
+        w0 *= oracle_fp_weight(0, m, d->path[m - 1]);
+        w1 *= oracle_fp_weight(1, m, d->path[m - 1]);
+    }
+    d->count += 1;
+    d->fp[0] += w0;
+    d->fp[1] += w1;
+    if (d->n_paths) {
+        int64_t idx = (*d->n_paths)++;
+        if (d->paths && idx < d->cap) {
+            int32_t *rec = d->paths + (size_t)idx * (d->K + 2);
+            rec[0] = d->t;
+            rec[1] = d->k;
+            for (int m = 0; m < d->K; m++) rec[2 + m] = m < d->k ? d->path[m] : -1;
+        }
+    }
+}
+
+static int hop(Dfs *d, int32_t f, int32_t g)
+{
+    if (d->F) return pair_visible(d->F, d->n, d->s, f, g);
+    return bit(d->M + (size_t)f * d->W, g);
+}
+
+static void dfs(Dfs *d, int depth)
+{
+    if (depth == d->k) {
+        if (bit(d->rx_row, d->path[depth - 1])) emit(d);
+        return;
+    }
+    for (int32_t g = 0; g < d->n; g++) {
+        if (depth == 0) {
+            if (!bit(d->tx_row, g)) continue;
+        } else if (!hop(d, d->path[depth - 1], g)) {
+            continue;
+        }
+        d->path[depth] = g;
+        dfs(d, depth + 1);
+    }
+}
+
+/* Image-tree summaries for snapshots [t0, t1): summary is (t1-t0) x (K+1) x 3
+ * u64 {count, fp0, fp1}; M is N x W; table is the full S x 2 x W; los is S.
+ * If n_paths is non-null, paths are counted into *n_paths (not reset here)
+ * and the first cap are written as records (t, k, f1..fK, -1 padded). */
+OR_EXPORT void oracle_tree(const uint32_t *M, const uint32_t *table, const uint8_t *los,
+                           int32_t n, int64_t t0, int64_t t1, int32_t K, uint64_t *summary,
+                           int32_t *paths, int64_t cap, int64_t *n_paths)
+{
+    int32_t W = oracle_words(n);
+    for (int64_t t = t0; t < t1; t++) {
+        uint64_t *sm = summary + (size_t)(t - t0) * (K + 1) * 3;
+        Dfs d;
+        memset(&d, 0, sizeof d);
+        d.M = M; d.n = n; d.W = W; d.t = (int32_t)t; d.K = K;
+        d.tx_row = table + (size_t)t * 2 * W;
+        d.rx_row = d.tx_row + W;
+        d.paths = paths; d.cap = cap; d.n_paths = n_paths;
+        /* order 0: the direct path */
+        sm[0] = sm[1] = sm[2] = los[t] ? 1 : 0;
+        if (n_paths && los[t]) {
+            d.k = 0;
+            emit(&d);
+            d.count = 0; d.fp[0] = d.fp[1] = 0;
+        }
+        for (int k = 1; k <= K; k++) {
+            d.k = k; d.count = 0; d.fp[0] = d.fp[1] = 0;
+            dfs(&d, 0);
+            sm[3 * k + 0] = d.count;
+            sm[3 * k + 1] = d.fp[0];
+            sm[3 * k + 2] = d.fp[1];
+        }
+    }
+}
+
+/* Step 7: the same summaries, with nothing cached: for each snapshot the Tx
+ * and Rx rows are computed from geometry, and every hop's visibility is
+ * recomputed from geometry when the search reaches it. */
+OR_EXPORT void oracle_traditional(const int32_t *facets, int32_t n, int32_t s, const int32_t *tx,
+                                  const int32_t *rx, int64_t t0, int64_t t1, int32_t K,
+                                  uint64_t *summary)
+{
+    int32_t W = oracle_words(n);
+    Facet *F = load_facets(facets, n, s);
+    uint32_t *rows = (uint32_t *)calloc((size_t)2 * W, sizeof(uint32_t));
+    for (int64_t t = t0; t < t1; t++) {
+        V X[2] = {point_of(tx + 3 * t, s), point_of(rx + 3 * t, s)};
+        memset(rows, 0, sizeof(uint32_t) * 2 * W);
+        for (int side = 0; side < 2; side++)
+            for (int32_t j = 0; j < n; j++)
+                if (point_sees(F, n, s, X[side], j)) rows[side * W + (j >> 5)] |= 1u << (j & 31);
+        uint64_t *sm = summary + (size_t)(t - t0) * (K + 1) * 3;
+        int l = !blocked(F, n, X[0], X[1]);
+        sm[0] = sm[1] = sm[2] = (uint64_t)l;
+        Dfs d;
+        memset(&d, 0, sizeof d);
+        d.n = n; d.W = W; d.t = (int32_t)t; d.K = K;
+        d.tx_row = rows; d.rx_row = rows + W;
+        d.F = F; d.s = s;
+        for (int k = 1; k <= K; k++) {
+            d.k = k; d.count = 0; d.fp[0] = d.fp[1] = 0;
+            dfs(&d, 0);
+            sm[3 * k + 0] = d.count;
+            sm[3 * k + 1] = d.fp[0];
+            sm[3 * k + 2] = d.fp[1];
+        }
+    }
+    free(rows);
+    free(F);
+}

@@ -1,0 +1,371 @@
+#!/usr/bin/env python
+"""Benchmark of the inter-visibility hot path on GB300.
+
+One step = one pass of the whole path over the district workload (1 km
+square, 200 box buildings, 1,001 facets, 5 x 5 samples per facet, 10,000
+Rx snapshots at 120 km/h every 1 ms, rooftop Tx, reflection order 3):
+ivm_build_matrix (ingest, BVH, facing screen, sample-pair occlusion),
+ivm_build_table (Tx and Rx rows and the direct path per snapshot) and
+ivm_expand_image_tree (orders 0..3, counts and fingerprints).
+
+Metric: visibility pair-tests per second: the N^2 ordered facet pairs the
+matrix decides plus the 2 N S Tx/Rx-facet pairs the table decides, per step,
+divided by the step time.  Snapshot tables per second (S / step time) is
+reported beside it.
+
+`value` is device time (CUDA events on the library's stream) with inputs
+resident in HBM; L2 is flushed between steps by writing a 512 MB buffer
+outside the timed events.  `e2e` is the same metric through the same C-ABI
+calls with pinned host buffers (every copy inside the timed region).
+`--impl reference` times the CPU oracle (the brute-force definition) on the
+host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "visibility pair-tests/s and Tx/Rx snapshot tables/s, bit-exact, vs plain GPU form"
+UNIT = "pair-tests/s"
+WORKLOAD = ("district: 1 km x 1 km, 200 box buildings (8-40 m footprint, 6-60 m high), "
+            "1,001 facets, 5x5 samples per facet, 10,000 Rx snapshots at 120 km/h every 1 ms, "
+            "rooftop Tx, reflection order <= 3, seed 2")
+FP32_OPS_PER_NODE_TEST = 30      # seg_box: 3 axes x 8 + 6 for the widening
+FP32_OPS_PER_FILTERED_LEAF = 104  # 4 edges x 26 (value, permanent, bound, compare)
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    return p.parse_args()
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", init_method="env://")
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(ws, v):
+    if ws == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------ clocks
+
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.path = tempfile.mktemp(suffix=".csv")
+        self.proc = None
+
+    def start(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.fh,
+                stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) >= 9:
+                rows.append(f)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ------------------------------------------------------------------ CPU oracle
+
+def oracle_sample(sc, n_rows, n_snaps, seed, threads):
+    """Oracle on a bounded sample of the workload; returns (pair tests, s)."""
+    import numpy as np
+
+    import oracle
+    rng = np.random.default_rng(seed)
+    rows = rng.choice(sc.n_facets, n_rows, replace=False)
+    snaps = rng.choice(sc.n_snap, n_snaps, replace=False)
+    t0 = time.perf_counter()
+    oracle.matrix(sc.facets, sc.samples_per_side, rows=rows, threads=threads)
+    oracle.table(sc.facets, sc.samples_per_side, sc.tx, sc.rx, snaps=snaps, threads=threads)
+    dt = time.perf_counter() - t0
+    units = n_rows * sc.n_facets + 2 * n_snaps * sc.n_facets
+    return units, dt
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return
+    import oracle
+    from paper_2501_02747_gb300 import scenegen as sg
+    oracle.build()
+    sc = sg.district()
+    threads = os.cpu_count() or 1
+    for k in range(args.warmup):
+        oracle_sample(sc, 1, 2, 100 + k, threads)
+    units = 0
+    secs = 0.0
+    for k in range(args.steps):
+        u, dt = oracle_sample(sc, 4, 16, 200 + k, threads)
+        units += u
+        secs += dt
+    value = units / secs
+    sample = (f"per step: 4 seeded matrix rows (4 x 1,001 ordered pairs) and 16 seeded "
+              f"snapshots (16 x 2 x 1,001 Tx/Rx-facet pairs) of the district workload")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int128",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "oracle": "brute force, every segment against every "
+                   "triangle, exact int128 (oracle/ivm_oracle.c)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+# ------------------------------------------------------------------ GPU arm
+
+def traffic_from_profiles(kernel):
+    """dram bytes per launch of `kernel` from profiles/, if taken on the current sources."""
+    from paper_2501_02747_gb300 import build
+    path = os.path.join(ROOT, "profiles", f"traffic_{kernel}.txt")
+    if not os.path.exists(path):
+        return None
+    kv = {}
+    for line in open(path):
+        if ":" in line and not line.startswith("#"):
+            k, v = line.split(":", 1)
+            kv[k.strip()] = v.strip()
+    if kv.get("source_digest") != build._digest():
+        return None
+    try:
+        return float(kv["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+def run_ours(args, ws, rank, local):
+    import numpy as np
+    import torch
+
+    from paper_2501_02747_gb300 import build, ivm
+    from paper_2501_02747_gb300 import scenegen as sg
+    build.build()
+    torch.cuda.set_device(local)
+    dev = f"cuda:{local}"
+    stream = torch.cuda.current_stream(local)
+    sc = sg.district()
+    N, S, K, s = sc.n_facets, sc.n_snap, sc.max_order, sc.samples_per_side
+    W = ivm.words(N)
+    units = N * N + 2 * N * S
+    ctx = ivm.Context(local, stream)
+    facets_d = torch.from_numpy(sc.facets).to(dev)
+    tx_d = torch.from_numpy(sc.tx).to(dev)
+    rx_d = torch.from_numpy(sc.rx).to(dev)
+    M_d = torch.empty((N, W), dtype=torch.int32, device=dev)
+    T_d = torch.empty((S, 2, W), dtype=torch.int32, device=dev)
+    L_d = torch.empty((S,), dtype=torch.uint8, device=dev)
+    summ_d = torch.empty((S, K + 1, 3), dtype=torch.int64, device=dev)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+
+    forms = {
+        "plain": dict(mode=ivm.IVM_MODE_EXACT, flags=0),
+        "fast": dict(mode=ivm.IVM_MODE_FILTERED, flags=ivm.IVM_FLAG_PERSISTENT),
+    }
+
+    def step(form, fac, tx, rx, M, T, L, summ):
+        kw = forms[form]
+        _, stm = ivm.ivm_build_matrix(ctx, fac, s, out=M, **kw)
+        _, stt = ivm.ivm_build_table(ctx, fac, s, tx, rx, out=(T, L), **kw)
+        ivm.ivm_expand_image_tree(ctx, M, T, L, N, K, summary=summ)
+        return stm, stt
+
+    def timed(form):
+        for _ in range(args.warmup):
+            step(form, facets_d, tx_d, rx_d, M_d, T_d, L_d, summ_d)
+        torch.cuda.synchronize()
+        barrier(ws)
+        torch.cuda.synchronize()
+        launches0 = ivm.kernel_launches()
+        times, kern = [], {"matrix": 0.0, "table": 0.0}
+        ops, node_tests, leaf_tests = {"matrix": 0, "table": 0}, 0, 0
+        stats = None
+        for _ in range(args.steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            stm, stt = step(form, facets_d, tx_d, rx_d, M_d, T_d, L_d, summ_d)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+            kern["matrix"] += stm.ms_traverse
+            kern["table"] += stt.ms_traverse
+            for name, st in (("matrix", stm), ("table", stt)):
+                leaf_fp = st.leaf_tests - st.exact_tests if forms[form]["mode"] else 0
+                ops[name] += st.node_tests * FP32_OPS_PER_NODE_TEST + \
+                    leaf_fp * FP32_OPS_PER_FILTERED_LEAF
+            stats = (stm.as_dict(), stt.as_dict())
+        launches = ivm.kernel_launches() - launches0
+        torch.cuda.synchronize()
+        barrier(ws)
+        ms = max_over_ranks(ws, sum(times)) / args.steps
+        return ms, kern, ops, launches, stats, times
+
+    clocks = Clocks(local)
+    ms_plain, kern_plain, ops_plain, _, stats_plain, _ = timed("plain")
+    clocks.start()
+    ms_fast, kern_fast, ops_fast, launches, stats_fast, times = timed("fast")
+    clk = clocks.stop()
+
+    # parity of the two forms on this step's outputs (cheap, outside timing)
+    step("plain", facets_d, tx_d, rx_d, M_d, T_d, L_d, summ_d)
+    ref = (M_d.clone(), T_d.clone(), L_d.clone(), summ_d.clone())
+    step("fast", facets_d, tx_d, rx_d, M_d, T_d, L_d, summ_d)
+    forms_agree = all(bool((a == b).all()) for a, b in zip(ref, (M_d, T_d, L_d, summ_d)))
+
+    value = ws * units / (ms_fast / 1e3)
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_fast, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int64/int128 + fp32 filter",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "form": "fast: FP32 filter + exact fallback, "
+                   "persistent work queue", "l2": "flushed between steps (512 MB write)",
+                   "facets": N, "snapshots": S, "samples_per_side": s, "max_order": K,
+                   "pair_tests_per_step": units},
+        "snapshot_tables_per_s": ws * S / (ms_fast / 1e3),
+        "plain": {"ms_per_step": ms_plain, "value": ws * units / (ms_plain / 1e3),
+                  "form": "exact int64/int128 facet tests, one warp per work item"},
+        "speedup_vs_plain": ms_plain / ms_fast,
+        "forms_bit_identical": forms_agree,
+        "gpu_launches": launches,
+        "clocks": clk,
+        "stats": {"matrix": stats_fast[0], "table": stats_fast[1]},
+    }
+    # roofline of the dominant kernel (FP32 issue of the traversal)
+    dom = "table" if kern_fast["table"] >= kern_fast["matrix"] else "matrix"
+    kname = {"table": "k_table", "matrix": "k_matrix"}[dom]
+    import json as _json
+    peaks = _json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) \
+        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    n_sm = torch.cuda.get_device_properties(local).multi_processor_count
+    peak = n_sm * 128 * sm_max * 1e6 / 1e12
+    achieved = ops_fast[dom] / (kern_fast[dom] / 1e3) / 1e12 if kern_fast[dom] > 0 else 0.0
+    out["roofline"] = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak,
+                       "unit": "Tops/s", "frac": achieved / peak if peak else None,
+                       "traffic": traffic_from_profiles(kname),
+                       "peak_basis": f"{n_sm} SMs x 128 FP32 lanes x {sm_max:.0f} MHz "
+                                     "(sm_max_mhz of MEASURED_PEAKS.json)",
+                       "ms_per_launch": kern_fast[dom] / args.steps,
+                       "ms_per_step_matrix": kern_fast["matrix"] / args.steps,
+                       "ms_per_step_table": kern_fast["table"] / args.steps}
+
+    if not args.no_e2e:
+        fac_h = torch.from_numpy(sc.facets).pin_memory()
+        tx_h = torch.from_numpy(sc.tx).pin_memory()
+        rx_h = torch.from_numpy(sc.rx).pin_memory()
+        M_h = torch.empty((N, W), dtype=torch.int32).pin_memory()
+        T_h = torch.empty((S, 2, W), dtype=torch.int32).pin_memory()
+        L_h = torch.empty((S,), dtype=torch.uint8).pin_memory()
+        summ_h = torch.empty((S, K + 1, 3), dtype=torch.int64).pin_memory()
+        for _ in range(max(1, args.warmup)):
+            step("fast", fac_h, tx_h, rx_h, M_h, T_h, L_h, summ_h)
+        torch.cuda.synchronize()
+        barrier(ws)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            step("fast", fac_h, tx_h, rx_h, M_h, T_h, L_h, summ_h)
+        torch.cuda.synchronize()
+        e2e_s = max_over_ranks(ws, time.perf_counter() - t0) / args.steps
+        h2d = 2 * fac_h.numel() * 4 + tx_h.numel() * 4 + rx_h.numel() * 4 + \
+            M_h.numel() * 4 + T_h.numel() * 4 + L_h.numel()
+        d2h = M_h.numel() * 4 + T_h.numel() * 4 + L_h.numel() + summ_h.numel() * 8
+        out["e2e"] = {"value": ws * units / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                      "d2h_bytes_per_step": d2h, "ms_per_step": 1e3 * e2e_s,
+                      "path": "same three C-ABI calls with pinned host buffers"}
+
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        threads = os.cpu_count() or 1
+        u, dt = oracle_sample(sc, 32, 96, 7, threads)
+        out["cpu_baseline"] = {"value": u / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+                               "sample": "32 seeded matrix rows and 96 seeded snapshots of the "
+                                         f"district workload ({u} pair tests, {dt:.1f} s)"}
+    ctx.close()
+    if rank == 0:
+        print(json.dumps(out))
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+    else:
+        run_ours(args, ws, rank, local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

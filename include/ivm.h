@@ -1,0 +1,181 @@
+/*
+ * ivm.h -- C ABI of the GB300 inter-visibility library.
+ *
+ * The library builds, on one GPU, the three products of the pre-processing
+ * method of Yang et al., "An Efficient Pre-Processing Method for 6G Dynamic
+ * Ray-Tracing Channel Modeling" (arXiv 2501.02747):
+ *
+ *   ivm_build_matrix       the static inter-visibility matrix over building
+ *                          facets (Sec. II: the intersection judgment between
+ *                          static objects is done once, in pre-processing);
+ *   ivm_build_table        the per-snapshot inter-visibility table of the
+ *                          mobile Tx and Rx (Sec. III-B/C, Table II);
+ *   ivm_expand_image_tree  the image-tree path sets read off the matrix and
+ *                          the table (Sec. II intro, Sec. III-B, Table II).
+ *
+ * Geometry.  Coordinates are int32 centimetres.  A facet is the
+ * parallelogram {o + a u + b v : a, b in [0,1]} with outward normal u x v.
+ * Internally every coordinate is multiplied by 2s (s = samples per side) so
+ * that the s x s cell-centre samples p_ab = 2s o + (2a+1) u + (2b+1) v are
+ * integers.  Range contract (else IVM_ERR_RANGE): every scaled corner
+ * coordinate and every scaled Tx/Rx coordinate has magnitude < 2^22; u x v is
+ * not zero; u x v divided by the gcd of its components fits in int32.
+ *
+ * Visibility rules (exact; no tolerance):
+ *   front(x, f)   <=> (u x v) . (x - 2s o) > 0, strict (Sec. II-B, Eq. (2):
+ *                     180 degrees or more counts as not visible);
+ *   blocked(P, Q) <=> some facet of the scene (closed) meets the open
+ *                     segment {P + l (Q - P) : 0 < l < 1};
+ *   M_ij = [i != j] and exists samples p of i, q of j: front(q, i) and
+ *          front(p, j) and not blocked(p, q)  (any free sample pair suffices:
+ *          partial visibility is visibility, Sec. III-A);
+ *   vis_X[t][j] = front(X_t, j) and exists sample q of j: not blocked(X_t, q)
+ *          for X in {Tx, Rx}; los[t] = not blocked(Tx_t, Rx_t).
+ *
+ * Bit rows.  A row of N bits is W = ceil(N / 32) uint32 words; bit j is word
+ * j >> 5, bit j & 31 (LSB first); padding bits are written as 0.
+ *
+ * Memory.  Every pointer argument may be host memory or device memory of the
+ * context's device; the library tells them apart with
+ * cudaPointerGetAttributes.  Host inputs are copied to the device and host
+ * outputs copied back inside the call.  The caller owns every buffer it
+ * passes; the context owns its scratch (scaled facets, BVH, pair lists,
+ * counters), which grows on demand and is freed by ivm_destroy.
+ *
+ * Streams and errors.  Work is enqueued on the stream given to ivm_create;
+ * every call synchronises that stream before it returns, so that device-side
+ * error words can be reported.  Calls return IVM_OK or a negative-free error
+ * code below; no exception crosses the ABI.  A context is used by one host
+ * thread at a time.
+ */
+#ifndef IVM_H
+#define IVM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------ error codes */
+#define IVM_OK 0
+#define IVM_ERR_ARG 1        /* null pointer, bad size or bad parameter */
+#define IVM_ERR_RANGE 2      /* geometry outside the range contract above */
+#define IVM_ERR_CAPACITY 3   /* path buffer too small; *n_paths_out = needed */
+#define IVM_ERR_TIMEOUT 4    /* a device-side iteration budget ran out */
+#define IVM_ERR_CUDA 5       /* a CUDA runtime call failed */
+#define IVM_ERR_INTERNAL 6   /* an internal invariant failed (stack depth) */
+
+/* ----------------------------------------------------------- forms (mode) */
+#define IVM_MODE_EXACT 0     /* exact integer facet tests */
+#define IVM_MODE_FILTERED 1  /* FP32 facet tests with a proven error bound,
+                                exact integer tests only when undecided */
+#define IVM_MODE_LEARNED 2   /* FILTERED + learned order of BVH clusters */
+
+/* ------------------------------------------------------------ flag bits */
+#define IVM_FLAG_PERSISTENT 1  /* persistent kernels over a work queue */
+#define IVM_FLAG_GRAPH 2       /* replay the call's launches as a CUDA graph */
+
+typedef struct ivm_facet {
+    int32_t o[3], u[3], v[3]; /* cm; u x v points outward */
+    int32_t building;         /* id carried through; -1 for the ground */
+} ivm_facet;                  /* 40 bytes */
+
+typedef struct ivm_scene {
+    const ivm_facet *facets;  /* host or device, n_facets records */
+    int32_t n_facets;         /* >= 1 */
+} ivm_scene;
+
+typedef struct ivm_params {
+    int32_t samples_per_side; /* s, 1..8 */
+    int32_t max_order;        /* K for ivm_expand_image_tree, 0..8 */
+    int32_t mode;             /* IVM_MODE_* */
+    int32_t tile;             /* pairs per work item (0 = autotuned / default) */
+    int32_t warps_per_block;  /* 0 = autotuned / default */
+    int32_t flags;            /* IVM_FLAG_* */
+} ivm_params;
+
+typedef struct ivm_stats {
+    uint64_t pairs;           /* ordered facet pairs decided (sum of N^2) */
+    uint64_t cand_pairs;      /* unordered pairs passing the facing screen */
+    uint64_t segments;        /* segments whose occlusion was tested */
+    uint64_t node_tests;      /* segment-vs-box tests */
+    uint64_t leaf_tests;      /* segment-vs-facet tests */
+    uint64_t undecided;       /* FP32 facet tests left undecided (FILTERED) */
+    uint64_t exact_tests;     /* facet tests decided by integer arithmetic */
+    uint64_t ranker_hits;     /* blocked segments whose occluder lay in the
+                                 ranker's first proposed cluster (LEARNED) */
+    float ms_ingest, ms_bvh, ms_screen, ms_traverse, ms_tree, ms_total;
+} ivm_stats;
+
+typedef struct ivm_tree_summary {
+    uint64_t count;           /* number of order-k paths */
+    uint64_t fp0, fp1;        /* sum over paths of prod_m h_c(m, f_m), mod 2^64 */
+} ivm_tree_summary;
+
+typedef struct ivm_ctx ivm_ctx;
+
+/* Create a context on `device`; `cuda_stream` is a cudaStream_t (NULL for
+ * the legacy default stream).  Errors: IVM_ERR_ARG, IVM_ERR_CUDA. */
+int ivm_create(ivm_ctx **out, int device, void *cuda_stream);
+
+/* Free the context and its scratch.  Accepts NULL. */
+int ivm_destroy(ivm_ctx *ctx);
+
+/* Inter-visibility matrix (Sec. II; the intersection judgment moved into
+ * pre-processing, Abstract and Sec. I).  For each scene k, matrix[k] receives
+ * N_k rows of W_k words, row i = facets visible from facet i; the matrix is
+ * symmetric with a zero diagonal.  n_scenes > 1 runs all scenes in one
+ * launch sequence (the batched form).  stats may be NULL.
+ * Errors: IVM_ERR_ARG (null pointers, n_scenes < 1, s outside 1..8),
+ * IVM_ERR_RANGE, IVM_ERR_TIMEOUT, IVM_ERR_INTERNAL, IVM_ERR_CUDA. */
+int ivm_build_matrix(ivm_ctx *ctx, const ivm_scene *scenes, int32_t n_scenes,
+                     const ivm_params *params, uint32_t *const *matrix, ivm_stats *stats);
+
+/* Inter-visibility table for specific points along the route (Sec. III-B/C,
+ * Table II).  For scene k: tx[k], rx[k] are [n_snap[k]][3] int32 cm;
+ * table[k] receives [n_snap[k]][2][W_k] words (row 0 the Tx's visible
+ * facets, row 1 the Rx's); los[k] receives n_snap[k] bytes, 1 if the direct
+ * Tx-Rx segment is free (1 when Tx_t = Rx_t).  The matrix is not an input:
+ * the table is defined by geometry, and the image tree combines the two.
+ * Errors: as ivm_build_matrix (IVM_ERR_RANGE also for a Tx/Rx position). */
+int ivm_build_table(ivm_ctx *ctx, const ivm_scene *scenes, int32_t n_scenes,
+                    const ivm_params *params, const int32_t *const *tx,
+                    const int32_t *const *rx, const int64_t *n_snap,
+                    uint32_t *const *table, uint8_t *const *los, ivm_stats *stats);
+
+/* Image-tree expansion (Sec. II intro; Sec. III-B, Table II: a path is
+ * transmitter -> reference face -> ... -> aim face).  For every snapshot t
+ * and order k = 0..max_order: summary[t][k] = {count, fp0, fp1} over the
+ * paths (f1..fk) with vis_Tx[t][f1], M[f_m][f_m+1] for each hop, and
+ * vis_Rx[t][fk]; order 0 is the direct path (count = fp0 = fp1 = los[t]).
+ * Fingerprint weights: h_c(m, f) = splitmix64(seed_c ^ (m << 32) ^ f) | 1
+ * with seed_0 = 0x243F6A8885A308D3, seed_1 = 0x13198A2E03707344 and
+ * splitmix64 the SplitMix64 output function (Steele, Lea, Flood 2014).
+ * matrix is [n_facets][W], table [n_snap][2][W], los [n_snap],
+ * summary [n_snap][max_order + 1].
+ * If paths is not NULL, path records int32 [path_capacity][max_order + 2] =
+ * (t, k, f1..fk, -1 padding) are written in lexicographic order of
+ * (t, k, f1, ..., fk); *n_paths_out (may be NULL) receives the total number
+ * of paths, whether or not they fit.  Errors: IVM_ERR_ARG,
+ * IVM_ERR_CAPACITY (the first path_capacity records are written),
+ * IVM_ERR_CUDA. */
+int ivm_expand_image_tree(ivm_ctx *ctx, const uint32_t *matrix, const uint32_t *table,
+                          const uint8_t *los, int32_t n_facets, int64_t n_snap,
+                          int32_t max_order, ivm_tree_summary *summary, int32_t *paths,
+                          int64_t path_capacity, int64_t *n_paths_out);
+
+/* Message for an error code (static string). */
+const char *ivm_strerror(int code);
+
+/* Diagnostic, not from the paper: number of CUDA kernels this library has
+ * launched in this process so far (all contexts and threads).  Lets a caller
+ * count the launches of a timed region without a profiler. */
+uint64_t ivm_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* IVM_H */

@@ -66,6 +66,14 @@ def lib():
         L.oracle_pair_free_count.argtypes = [_i32p, ctypes.c_int32, ctypes.c_int32,
                                              ctypes.c_int32, ctypes.c_int32]
         L.oracle_pair_free_count.restype = ctypes.c_int64
+        L.oracle_pair_visible.argtypes = [_i32p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                          ctypes.c_int32]
+        L.oracle_pair_visible.restype = ctypes.c_int
+        L.oracle_point_sees.argtypes = [_i32p, ctypes.c_int32, ctypes.c_int32, _i32p,
+                                        ctypes.c_int32]
+        L.oracle_point_sees.restype = ctypes.c_int
+        L.oracle_los.argtypes = [_i32p, ctypes.c_int32, ctypes.c_int32, _i32p, _i32p]
+        L.oracle_los.restype = ctypes.c_int
         L.oracle_splitmix64.argtypes = [ctypes.c_uint64]
         L.oracle_splitmix64.restype = ctypes.c_uint64
         L.oracle_fp_weight.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]
@@ -105,6 +113,46 @@ def blocked(facets, s, P, Q) -> bool:
 def pair_free_count(facets, s, i, j) -> int:
     F = _facets(facets)
     return int(lib().oracle_pair_free_count(_p(F, _i32p), F.shape[0], s, i, j))
+
+
+def pair_entries(facets, s, pairs, threads=None) -> np.ndarray:
+    """M_ij for each (i, j) in pairs: uint8 [len(pairs)]."""
+    F = _facets(facets)
+    L = lib()
+    pairs = [(int(i), int(j)) for i, j in pairs]
+    with ThreadPoolExecutor(_threads(threads)) as ex:
+        out = list(ex.map(lambda p: L.oracle_pair_visible(_p(F, _i32p), F.shape[0], s, *p), pairs))
+    return np.asarray(out, dtype=np.uint8)
+
+
+def table_entries(facets, s, points, facet_ids, threads=None) -> np.ndarray:
+    """vis of point X (cm) towards facet j for each (X, j): uint8 [len]."""
+    F = _facets(facets)
+    L = lib()
+    pts = np.ascontiguousarray(points, dtype=np.int32).reshape(-1, 3)
+    ids = [int(j) for j in facet_ids]
+
+    def one(k):
+        return L.oracle_point_sees(_p(F, _i32p), F.shape[0], s, _p(pts[k], _i32p), ids[k])
+
+    with ThreadPoolExecutor(_threads(threads)) as ex:
+        out = list(ex.map(one, range(len(ids))))
+    return np.asarray(out, dtype=np.uint8)
+
+
+def los_entries(facets, s, A, B, threads=None) -> np.ndarray:
+    """not blocked(A_k, B_k) for each k (points in cm): uint8 [len]."""
+    F = _facets(facets)
+    L = lib()
+    A = np.ascontiguousarray(A, dtype=np.int32).reshape(-1, 3)
+    B = np.ascontiguousarray(B, dtype=np.int32).reshape(-1, 3)
+
+    def one(k):
+        return L.oracle_los(_p(F, _i32p), F.shape[0], s, _p(A[k], _i32p), _p(B[k], _i32p))
+
+    with ThreadPoolExecutor(_threads(threads)) as ex:
+        out = list(ex.map(one, range(A.shape[0])))
+    return np.asarray(out, dtype=np.uint8)
 
 
 def matrix(facets, s, rows=None, threads=None) -> np.ndarray:

@@ -249,6 +249,35 @@ OR_EXPORT int oracle_blocked(const int32_t *facets, int32_t n, int32_t s, const 
     return r;
 }
 
+/* Single entries, for sampled checks at sizes where whole rows are too slow:
+ * M_ij, vis of the point X (cm, unscaled) towards facet j, and the direct
+ * segment between two points (cm). */
+OR_EXPORT int oracle_pair_visible(const int32_t *facets, int32_t n, int32_t s, int32_t i, int32_t j)
+{
+    Facet *F = load_facets(facets, n, s);
+    int r = pair_visible(F, n, s, i, j);
+    free(F);
+    return r;
+}
+
+OR_EXPORT int oracle_point_sees(const int32_t *facets, int32_t n, int32_t s, const int32_t *X,
+                                int32_t j)
+{
+    Facet *F = load_facets(facets, n, s);
+    int r = point_sees(F, n, s, point_of(X, s), j);
+    free(F);
+    return r;
+}
+
+OR_EXPORT int oracle_los(const int32_t *facets, int32_t n, int32_t s, const int32_t *A,
+                         const int32_t *B)
+{
+    Facet *F = load_facets(facets, n, s);
+    int r = !blocked(F, n, point_of(A, s), point_of(B, s));
+    free(F);
+    return r;
+}
+
 /* Number of sample pairs (p_a on i, q_b on j) that satisfy the three
  * conditions of step 4 (for the hand-counted partial-blocker scene). */
 OR_EXPORT int64_t oracle_pair_free_count(const int32_t *facets, int32_t n, int32_t s, int32_t i,

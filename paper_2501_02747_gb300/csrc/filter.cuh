@@ -1,0 +1,91 @@
+// filter.cuh -- FP32 facet test with a proven error bound (the precision
+// form).  It returns exactly what facet_hit_exact returns; the integer
+// arithmetic runs only for edge orientations the float value cannot decide.
+//
+// Plane sides stay exact in int64 (three 32x32->64 products, cheap).  The four
+// edge orientations e = d . (a x b), with a, b, d integer vectors below 2^23
+// (exact in float), are evaluated as
+//   c_i = fl(fl(p_i) - fl(q_i))          (p_i, q_i the two products of a x b)
+//   e~  = fl(fl(fl(c_x d_x) + fl(c_y d_y)) + fl(c_z d_z))
+// with round-to-nearest intrinsics (never contracted into FMAs).  With
+// u = 2^-24 and m_i = |p_i| + |q_i|, standard rounding-error analysis gives
+//   |fl(c_i) - c_i| <= (2u + u^2) m_i,
+//   |e~ - sum d_i fl(c_i)| <= gamma_3 sum |d_i| |fl(c_i)|,
+// so |e~ - e| <= (5u + O(u^2)) M with M = sum_i |d_i| m_i.  M' is M computed
+// from |fl(p_i)|, |fl(q_i)| with round-up additions and products, so
+// M <= M' / (1 - u), and |e~ - e| < 6u M' < 2^-21 M'.  When |e~| > 2^-21 M',
+// sign(e~) = sign(e).  Inputs are integers, so no product underflows; all
+// magnitudes stay below 2^75, far from overflow.
+#pragma once
+
+#include "traverse.cuh"
+
+namespace ivm {
+
+// +1 / -1 when the float value decides the sign, 0 when it cannot.
+__device__ __forceinline__ int orient_filtered(float ax, float ay, float az, float bx, float by,
+                                               float bz, float dx, float dy, float dz)
+{
+    float p1 = __fmul_rn(ay, bz), q1 = __fmul_rn(az, by);
+    float p2 = __fmul_rn(az, bx), q2 = __fmul_rn(ax, bz);
+    float p3 = __fmul_rn(ax, by), q3 = __fmul_rn(ay, bx);
+    float cx = __fsub_rn(p1, q1), cy = __fsub_rn(p2, q2), cz = __fsub_rn(p3, q3);
+    float e = __fadd_rn(__fadd_rn(__fmul_rn(cx, dx), __fmul_rn(cy, dy)), __fmul_rn(cz, dz));
+    float m1 = __fadd_ru(fabsf(p1), fabsf(q1));
+    float m2 = __fadd_ru(fabsf(p2), fabsf(q2));
+    float m3 = __fadd_ru(fabsf(p3), fabsf(q3));
+    float M = __fadd_ru(__fadd_ru(__fmul_ru(fabsf(dx), m1), __fmul_ru(fabsf(dy), m2)),
+                        __fmul_ru(fabsf(dz), m3));
+    float bound = M * 0x1p-21f;   // exact: power-of-two scaling of a value >= 1 or 0
+    return e > bound ? 1 : (e < -bound ? -1 : 0);
+}
+
+__device__ __forceinline__ bool facet_hit_filtered(const Seg &s, const Leaf &L, WalkCounters &wc)
+{
+    long long rx = s.px - L.ox, ry = s.py - L.oy, rz = s.pz - L.oz;
+    long long sp = (long long)L.nx * rx + (long long)L.ny * ry + (long long)L.nz * rz;
+    long long sd = (long long)L.nx * s.dx + (long long)L.ny * s.dy + (long long)L.nz * s.dz;
+    int a = sgn_ll(sp), b = sgn_ll(sp + sd);
+    if (a == b) {
+        if (a != 0) return false;
+        wc.exact++;
+        return coplanar_hit(s, L);
+    }
+    if (a == 0 || b == 0) return false;
+    int c0x = L.ox - s.px, c0y = L.oy - s.py, c0z = L.oz - s.pz;
+    int c1x = c0x + L.ux, c1y = c0y + L.uy, c1z = c0z + L.uz;
+    int c2x = c1x + L.vx, c2y = c1y + L.vy, c2z = c1z + L.vz;
+    int c3x = c0x + L.vx, c3y = c0y + L.vy, c3z = c0z + L.vz;
+    float f0x = (float)c0x, f0y = (float)c0y, f0z = (float)c0z;
+    float f1x = (float)c1x, f1y = (float)c1y, f1z = (float)c1z;
+    float f2x = (float)c2x, f2y = (float)c2y, f2z = (float)c2z;
+    float f3x = (float)c3x, f3y = (float)c3y, f3z = (float)c3z;
+    float dx = (float)s.dx, dy = (float)s.dy, dz = (float)s.dz;
+    int e0 = orient_filtered(f0x, f0y, f0z, f1x, f1y, f1z, dx, dy, dz);
+    int e1 = orient_filtered(f1x, f1y, f1z, f2x, f2y, f2z, dx, dy, dz);
+    int e2 = orient_filtered(f2x, f2y, f2z, f3x, f3y, f3z, dx, dy, dz);
+    int e3 = orient_filtered(f3x, f3y, f3z, f0x, f0y, f0z, dx, dy, dz);
+    bool pos = (e0 > 0) | (e1 > 0) | (e2 > 0) | (e3 > 0);
+    bool neg = (e0 < 0) | (e1 < 0) | (e2 < 0) | (e3 < 0);
+    if (pos & neg) return false;
+    if ((e0 != 0) & (e1 != 0) & (e2 != 0) & (e3 != 0)) return true;
+    // some edge is undecided and the decided ones agree: settle it exactly
+    wc.undecided++;
+    wc.exact++;
+    if (e0 == 0) e0 = orient_sign(c0x, c0y, c0z, c1x, c1y, c1z, s.dx, s.dy, s.dz);
+    if (e1 == 0) e1 = orient_sign(c1x, c1y, c1z, c2x, c2y, c2z, s.dx, s.dy, s.dz);
+    if (e2 == 0) e2 = orient_sign(c2x, c2y, c2z, c3x, c3y, c3z, s.dx, s.dy, s.dz);
+    if (e3 == 0) e3 = orient_sign(c3x, c3y, c3z, c0x, c0y, c0z, s.dx, s.dy, s.dz);
+    bool nonneg = (e0 >= 0) & (e1 >= 0) & (e2 >= 0) & (e3 >= 0);
+    bool nonpos = (e0 <= 0) & (e1 <= 0) & (e2 <= 0) & (e3 <= 0);
+    return nonneg | nonpos;
+}
+
+struct FilteredLeaf {
+    __device__ __forceinline__ bool operator()(const Seg &s, const Leaf &L, WalkCounters &wc) const
+    {
+        return facet_hit_filtered(s, L, wc);
+    }
+};
+
+}  // namespace ivm

@@ -1,0 +1,122 @@
+// matrix.cu -- the 3D inter-visibility matrix (Sec. II of the paper).
+//
+// M_ij = 1 when some sample p of facet i and some sample q of facet j see
+// each other: q strictly in front of i, p strictly in front of j (Sec. II-B,
+// Eq. (2)), and no facet meets the open segment p-q (the intersection
+// judgment moved into pre-processing, Abstract and Sec. I).  The Tx plays no
+// part (Sec. II-B: Tx-to-reference-face visibility is assumed).
+//
+// One warp decides one candidate pair (i < j).  Its lanes take the s^4 sample
+// pairs 32 at a time as a packet; a packet ends as soon as every lane is
+// blocked, and the pair ends at the first packet with a free lane.  The bit
+// is written to row i and, by symmetry, row j.
+#include "ivm_internal.cuh"
+#include "traverse.cuh"
+#include "filter.cuh"
+
+namespace ivm {
+
+template <class LeafFn>
+__device__ __forceinline__ void decide_pair(const DevScenes &g, int gi, int gj, int *err,
+                                            WalkCounters &wc, LeafFn leaf)
+{
+    const int lane = threadIdx.x & 31;
+    const Leaf Li = load_leaf(g.leaf, gi), Lj = load_leaf(g.leaf, gj);
+    const SceneDesc &D = g.desc[Li.scene];
+    const int s = D.s, s2 = s * s, total = s2 * s2;
+    const int i = gi - D.facet0, j = gj - D.facet0;
+    const int baseI = D.sample0 + i * s2, baseJ = D.sample0 + j * s2;
+    const float dirx = (float)(2 * (Lj.ox - Li.ox) + Lj.ux + Lj.vx - Li.ux - Li.vx);
+    const float diry = (float)(2 * (Lj.oy - Li.oy) + Lj.uy + Lj.vy - Li.uy - Li.vy);
+    const float dirz = (float)(2 * (Lj.oz - Li.oz) + Lj.uz + Lj.vz - Li.uz - Li.vz);
+    const int budget = 4 * D.n + 16;
+    bool visible = false;
+    for (int b0 = 0; b0 < total; b0 += 32) {
+        const int idx = b0 + lane;
+        const bool valid = idx < total;
+        const int a = valid ? idx / s2 : 0, b = valid ? idx - a * s2 : 0;
+        int px = 0, py = 0, pz = 0, qx = 0, qy = 0, qz = 0;
+        if (valid) {
+            px = __ldg(g.sx + baseI + a); py = __ldg(g.sy + baseI + a); pz = __ldg(g.sz + baseI + a);
+            qx = __ldg(g.sx + baseJ + b); qy = __ldg(g.sy + baseJ + b); qz = __ldg(g.sz + baseJ + b);
+        }
+        const bool face = valid && front_of(Lj, px, py, pz) && front_of(Li, qx, qy, qz);
+        unsigned alive = __ballot_sync(kFull, face);
+        if (!alive) continue;
+        wc.segments += face;
+        const Seg sg = make_seg(px, py, pz, qx, qy, qz);
+        alive = walk_packet(sg, alive, g.nodes, g.leaf, D.root, dirx, diry, dirz, budget, err,
+                            wc, leaf);
+        if (alive) {
+            visible = true;
+            break;
+        }
+    }
+    if (visible && lane == 0) {
+        atomicOr(D.matrix + (size_t)i * D.W + (j >> 5), 1u << (j & 31));
+        atomicOr(D.matrix + (size_t)j * D.W + (i >> 5), 1u << (i & 31));
+    }
+}
+
+template <bool PERSIST, class LeafFn>
+__global__ void k_matrix(DevScenes g, const int2 *pairs, unsigned long long npairs, int tile,
+                         unsigned long long *work, unsigned long long *ctr, int *err)
+{
+    WalkCounters wc;
+    LeafFn leaf;
+    const int lane = threadIdx.x & 31;
+    if (!PERSIST) {
+        unsigned long long w = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+        if (w < npairs) {
+            const int2 p = pairs[w];
+            decide_pair(g, p.x, p.y, err, wc, leaf);
+        }
+    } else {
+        for (;;) {
+            unsigned long long base = 0;
+            if (lane == 0) base = atomicAdd(work, (unsigned long long)tile);
+            base = __shfl_sync(kFull, base, 0);
+            if (base >= npairs) break;
+            unsigned long long end = min(base + (unsigned long long)tile, npairs);
+            for (unsigned long long w = base; w < end; w++) {
+                const int2 p = pairs[w];
+                decide_pair(g, p.x, p.y, err, wc, leaf);
+            }
+        }
+    }
+    flush_counters(wc, ctr);
+}
+
+template <class LeafFn>
+static cudaError_t launch_matrix_t(const DevScenes &g, const int2 *pairs,
+                                   unsigned long long npairs, const LaunchCfg &cfg,
+                                   unsigned long long *work, unsigned long long *ctr, int *err,
+                                   cudaStream_t st)
+{
+    const int threads = 32 * cfg.warps_per_block;
+    if (npairs == 0) return cudaSuccess;
+    if (cfg.persistent) {
+        int per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_matrix<true, LeafFn>, threads, 0);
+        int blocks = cfg.n_sm * (per_sm > 0 ? per_sm : 1);
+        cudaMemsetAsync(work, 0, sizeof(unsigned long long), st);
+        k_matrix<true, LeafFn><<<blocks, threads, 0, st>>>(g, pairs, npairs, cfg.tile, work, ctr, err);
+    } else {
+        unsigned long long blocks = (npairs + cfg.warps_per_block - 1) / cfg.warps_per_block;
+        k_matrix<false, LeafFn><<<(unsigned)blocks, threads, 0, st>>>(g, pairs, npairs, 1, work, ctr,
+                                                                     err);
+    }
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_matrix(const DevScenes &g, const int2 *pairs, unsigned long long npairs,
+                          const LaunchCfg &cfg, unsigned long long *work,
+                          unsigned long long *ctr, int *err, cudaStream_t st)
+{
+    if (cfg.mode == IVM_MODE_EXACT)
+        return launch_matrix_t<ExactLeaf>(g, pairs, npairs, cfg, work, ctr, err, st);
+    return launch_matrix_t<FilteredLeaf>(g, pairs, npairs, cfg, work, ctr, err, st);
+}
+
+}  // namespace ivm

@@ -1,0 +1,226 @@
+// table.cu -- the 3D inter-visibility table for the mobile Tx and Rx at the
+// specific points of their routes (Sec. III-B/C, Table II of the paper).
+//
+// vis_X[t][j] = 1 when facet j faces X_t strictly and some sample of j is
+// reachable from X_t by a segment no facet blocks; los[t] = 1 when the direct
+// Tx_t - Rx_t segment is free (Sec. III-B: the transmitter is the parent node
+// that searches its reference faces).
+//
+// One warp per (snapshot, side).  It screens 32 facets per step with one
+// facing test per lane, then takes the front-facing facets a packet at a
+// time: with s*s <= 32 samples, floor(32 / (s*s)) facets share a packet; with
+// more samples a facet takes several packets and stops at the first free one.
+// Each 32-facet word of the row is written once, by lane 0.
+#include "ivm_internal.cuh"
+#include "traverse.cuh"
+#include "filter.cuh"
+
+namespace ivm {
+
+__device__ __forceinline__ int scene_of_snap(const SceneDesc *desc, int n_scenes, long long T)
+{
+    int lo = 0, hi = n_scenes - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (desc[mid].snap0 <= T) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ int scene_of_los(const SceneDesc *desc, int n_scenes, long long c)
+{
+    int lo = 0, hi = n_scenes - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (desc[mid].los0 <= c) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ bool in_range(long long x, long long y, long long z)
+{
+    return (x > -kCoordLimit) & (x < kCoordLimit) & (y > -kCoordLimit) & (y < kCoordLimit) &
+           (z > -kCoordLimit) & (z < kCoordLimit);
+}
+
+template <class LeafFn>
+__device__ __forceinline__ void table_item(const DevScenes &g, long long item, int *err,
+                                           WalkCounters &wc, LeafFn leaf)
+{
+    const int lane = threadIdx.x & 31;
+    const long long T = item >> 1;
+    const int side = (int)(item & 1);
+    const int sc = scene_of_snap(g.desc, g.n_scenes, T);
+    const SceneDesc &D = g.desc[sc];
+    const long long t = T - D.snap0;
+    const int *src = (side ? D.rx : D.tx) + 3 * t;
+    const long long k = 2LL * D.s;
+    const long long X0 = k * src[0], X1 = k * src[1], X2 = k * src[2];
+    uint32_t *row = D.table + ((size_t)t * 2 + side) * D.W;
+    if (!in_range(X0, X1, X2)) {
+        if (lane == 0) raise_error(err, IVM_ERR_RANGE);
+        for (int c = lane; c < D.W; c += 32) row[c] = 0u;
+        return;
+    }
+    const int x = (int)X0, y = (int)X1, z = (int)X2;
+    const int s2 = D.s * D.s;
+    const int budget = 4 * D.n + 16;
+    for (int c = 0; c < D.W; c++) {
+        const int jl = 32 * c + lane;
+        bool fr = false;
+        if (jl < D.n) fr = front_of(load_leaf(g.leaf, D.facet0 + jl), x, y, z);
+        unsigned fm = __ballot_sync(kFull, fr);
+        unsigned word = 0;
+        while (fm) {
+            if (s2 <= 32) {
+                const int G = 32 / s2;
+                const int cnt = min(G, __popc(fm));
+                const int gi = lane / s2, b = lane - gi * s2;
+                const bool mine = gi < cnt;
+                unsigned m = fm;
+                for (int q = 0; q < gi && q < 31; q++) m &= m - 1;
+                const int jbit = mine ? __ffs(m) - 1 : 0;
+                const int gf = D.facet0 + 32 * c + jbit;
+                const int sidx = D.sample0 + (32 * c + jbit) * s2 + b;
+                int qx = 0, qy = 0, qz = 0;
+                if (mine) { qx = __ldg(g.sx + sidx); qy = __ldg(g.sy + sidx); qz = __ldg(g.sz + sidx); }
+                unsigned alive = __ballot_sync(kFull, mine);
+                const int lead = __shfl_sync(kFull, gf, 0);
+                const Leaf Lf = load_leaf(g.leaf, lead);
+                const float dirx = (float)(2 * Lf.ox + Lf.ux + Lf.vx - 2 * x);
+                const float diry = (float)(2 * Lf.oy + Lf.uy + Lf.vy - 2 * y);
+                const float dirz = (float)(2 * Lf.oz + Lf.uz + Lf.vz - 2 * z);
+                wc.segments += mine;
+                const Seg sg = make_seg(x, y, z, qx, qy, qz);
+                alive = walk_packet(sg, alive, g.nodes, g.leaf, D.root, dirx, diry, dirz, budget,
+                                    err, wc, leaf);
+                const unsigned smask = (s2 == 32) ? kFull : ((1u << s2) - 1u);
+                const bool gvis = mine && ((alive >> (gi * s2)) & smask) != 0u;
+                const unsigned bitv = (gvis && b == 0) ? (1u << jbit) : 0u;
+                word |= __reduce_or_sync(kFull, bitv);
+                for (int q = 0; q < cnt; q++) fm &= fm - 1;
+            } else {
+                const int jbit = __ffs(fm) - 1;
+                fm &= fm - 1;
+                const int jlocal = 32 * c + jbit;
+                const Leaf Lf = load_leaf(g.leaf, D.facet0 + jlocal);
+                const float dirx = (float)(2 * Lf.ox + Lf.ux + Lf.vx - 2 * x);
+                const float diry = (float)(2 * Lf.oy + Lf.uy + Lf.vy - 2 * y);
+                const float dirz = (float)(2 * Lf.oz + Lf.uz + Lf.vz - 2 * z);
+                for (int b0 = 0; b0 < s2; b0 += 32) {
+                    const int b = b0 + lane;
+                    const bool mine = b < s2;
+                    const int sidx = D.sample0 + jlocal * s2 + b;
+                    int qx = 0, qy = 0, qz = 0;
+                    if (mine) { qx = __ldg(g.sx + sidx); qy = __ldg(g.sy + sidx); qz = __ldg(g.sz + sidx); }
+                    unsigned alive = __ballot_sync(kFull, mine);
+                    wc.segments += mine;
+                    const Seg sg = make_seg(x, y, z, qx, qy, qz);
+                    alive = walk_packet(sg, alive, g.nodes, g.leaf, D.root, dirx, diry, dirz,
+                                        budget, err, wc, leaf);
+                    if (alive) {
+                        word |= 1u << jbit;
+                        break;
+                    }
+                }
+            }
+        }
+        if (lane == 0) row[c] = word;
+    }
+}
+
+template <class LeafFn>
+__device__ __forceinline__ void los_item(const DevScenes &g, long long chunk, int *err,
+                                         WalkCounters &wc, LeafFn leaf)
+{
+    const int lane = threadIdx.x & 31;
+    const int sc = scene_of_los(g.desc, g.n_scenes, chunk);
+    const SceneDesc &D = g.desc[sc];
+    const long long t = (chunk - D.los0) * 32 + lane;
+    const bool valid = t < D.nsnap;
+    const long long k = 2LL * D.s;
+    long long a0 = 0, a1 = 0, a2 = 0, b0 = 0, b1 = 0, b2 = 0;
+    if (valid) {
+        a0 = k * D.tx[3 * t]; a1 = k * D.tx[3 * t + 1]; a2 = k * D.tx[3 * t + 2];
+        b0 = k * D.rx[3 * t]; b1 = k * D.rx[3 * t + 1]; b2 = k * D.rx[3 * t + 2];
+    }
+    const bool ok = in_range(a0, a1, a2) & in_range(b0, b1, b2);
+    if (valid && !ok) raise_error(err, IVM_ERR_RANGE);
+    const bool same = (a0 == b0) & (a1 == b1) & (a2 == b2);
+    const bool test = valid && ok && !same;
+    unsigned alive = __ballot_sync(kFull, test);
+    wc.segments += test;
+    const Seg sg = make_seg((int)a0, (int)a1, (int)a2, (int)b0, (int)b1, (int)b2);
+    const int lead = __ffs(alive | 1u) - 1;
+    const float dirx = (float)__shfl_sync(kFull, sg.dx, lead);
+    const float diry = (float)__shfl_sync(kFull, sg.dy, lead);
+    const float dirz = (float)__shfl_sync(kFull, sg.dz, lead);
+    if (alive)
+        alive = walk_packet(sg, alive, g.nodes, g.leaf, D.root, dirx, diry, dirz, 4 * D.n + 16,
+                            err, wc, leaf);
+    if (valid) D.los[t] = (uint8_t)((ok && same) || ((alive >> lane) & 1u));
+}
+
+// Items [0, 2 * total_snap) are table rows; items after them are LoS chunks.
+template <bool PERSIST, class LeafFn>
+__global__ void k_table(DevScenes g, long long total_snap, long long total_items, int tile,
+                        unsigned long long *work, unsigned long long *ctr, int *err)
+{
+    WalkCounters wc;
+    LeafFn leaf;
+    const int lane = threadIdx.x & 31;
+    const long long rows = 2 * total_snap;
+    auto run = [&](long long it) {
+        if (it < rows) table_item(g, it, err, wc, leaf);
+        else los_item(g, it - rows, err, wc, leaf);
+    };
+    if (!PERSIST) {
+        long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+        if (w < total_items) run(w);
+    } else {
+        for (;;) {
+            unsigned long long base = 0;
+            if (lane == 0) base = atomicAdd(work, (unsigned long long)tile);
+            base = __shfl_sync(kFull, base, 0);
+            if ((long long)base >= total_items) break;
+            long long end = min((long long)base + tile, total_items);
+            for (long long it = (long long)base; it < end; it++) run(it);
+        }
+    }
+    flush_counters(wc, ctr);
+}
+
+template <class LeafFn>
+static cudaError_t launch_table_t(const DevScenes &g, long long total_snap, long long los_chunks,
+                                  const LaunchCfg &cfg, unsigned long long *work,
+                                  unsigned long long *ctr, int *err, cudaStream_t st)
+{
+    const long long items = 2 * total_snap + los_chunks;
+    if (items == 0) return cudaSuccess;
+    const int threads = 32 * cfg.warps_per_block;
+    if (cfg.persistent) {
+        int per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_table<true, LeafFn>, threads, 0);
+        int blocks = cfg.n_sm * (per_sm > 0 ? per_sm : 1);
+        cudaMemsetAsync(work, 0, sizeof(unsigned long long), st);
+        k_table<true, LeafFn><<<blocks, threads, 0, st>>>(g, total_snap, items, cfg.tile, work,
+                                                         ctr, err);
+    } else {
+        long long blocks = (items + cfg.warps_per_block - 1) / cfg.warps_per_block;
+        k_table<false, LeafFn><<<(unsigned)blocks, threads, 0, st>>>(g, total_snap, items, 1, work,
+                                                                    ctr, err);
+    }
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_table(const DevScenes &g, long long total_snap, long long total_los_chunks,
+                         const LaunchCfg &cfg, unsigned long long *work,
+                         unsigned long long *ctr, int *err, cudaStream_t st)
+{
+    if (cfg.mode == IVM_MODE_EXACT)
+        return launch_table_t<ExactLeaf>(g, total_snap, total_los_chunks, cfg, work, ctr, err, st);
+    return launch_table_t<FilteredLeaf>(g, total_snap, total_los_chunks, cfg, work, ctr, err, st);
+}
+
+}  // namespace ivm

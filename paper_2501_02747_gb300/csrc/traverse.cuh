@@ -1,0 +1,276 @@
+// traverse.cuh -- the occlusion test ("intersection judgment", Abstract and
+// Sec. II-B of the paper) on the GPU: a segment against the closed facets of
+// a scene, through its BVH, one warp at a time.
+//
+// A warp holds a packet of up to 32 segments (one per lane) that start and end
+// near each other (sample pairs of one facet pair, or samples of one facet
+// seen from one point).  The warp walks the BVH together: a node is entered
+// when any still-unblocked lane's segment touches the node's box, and a lane
+// drops out of the packet at the first facet that blocks it.  The walk stops
+// early when every lane is blocked.
+//
+// Exactness.  Box tests only cull: they are conservative (a box the segment
+// touches is never culled; a near miss may be kept).  Every facet decision is
+// exact: integer plane sides and edge orientations (int64 / int128), or the
+// FP32 filter of filter.cuh that falls back to them when it cannot decide.
+#pragma once
+
+#include "ivm_internal.cuh"
+
+namespace ivm {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr float kBig = 3.0e38f;
+
+// One lane's segment P -> Q = P + d (scaled integer coordinates).
+struct Seg {
+    int px, py, pz;
+    int dx, dy, dz;
+    float fpx, fpy, fpz;  // P as float: exact, |P| < 2^22
+    float ix, iy, iz;     // round-to-nearest reciprocal of d (0 where d == 0)
+    int zmask;            // bit a set where d_a == 0
+};
+
+__device__ __forceinline__ Seg make_seg(int px, int py, int pz, int qx, int qy, int qz)
+{
+    Seg s;
+    s.px = px; s.py = py; s.pz = pz;
+    s.dx = qx - px; s.dy = qy - py; s.dz = qz - pz;
+    s.fpx = (float)px; s.fpy = (float)py; s.fpz = (float)pz;
+    s.zmask = (s.dx == 0) | ((s.dy == 0) << 1) | ((s.dz == 0) << 2);
+    s.ix = s.dx ? __frcp_rn((float)s.dx) : 0.f;
+    s.iy = s.dy ? __frcp_rn((float)s.dy) : 0.f;
+    s.iz = s.dz ? __frcp_rn((float)s.dz) : 0.f;
+    return s;
+}
+
+// One axis of the slab test.  (l - p) is exact (integers below 2^24); the
+// product with the rounded reciprocal has relative error below 2^-23.
+__device__ __forceinline__ void slab_axis(float p, float inv, bool zero, float l, float h,
+                                          float &tn, float &tf)
+{
+    float t0 = __fmul_rn(l - p, inv), t1 = __fmul_rn(h - p, inv);
+    float n = fminf(t0, t1), f = fmaxf(t0, t1);
+    if (zero) {
+        bool in = (l <= p) & (p <= h);
+        n = in ? -kBig : kBig;
+        f = in ? kBig : -kBig;
+    }
+    tn = fmaxf(tn, n);
+    tf = fminf(tf, f);
+}
+
+// Conservative: true whenever the open segment touches the closed box.  The
+// entry/exit parameters carry relative error below 2^-23; widening them by
+// 2^-20 of their magnitude makes the test a superset of the exact one.
+__device__ __forceinline__ bool seg_box(const Seg &s, float lx, float ly, float lz, float hx,
+                                        float hy, float hz)
+{
+    float tn = -kBig, tf = kBig;
+    slab_axis(s.fpx, s.ix, s.zmask & 1, lx, hx, tn, tf);
+    slab_axis(s.fpy, s.iy, s.zmask & 2, ly, hy, tn, tf);
+    slab_axis(s.fpz, s.iz, s.zmask & 4, lz, hz, tn, tf);
+    float tnw = tn - fabsf(tn) * 0x1p-20f;
+    float tfw = tf + fabsf(tf) * 0x1p-20f;
+    return (tnw <= tfw) & (tnw < 1.f) & (tfw > 0.f);
+}
+
+// ------------------------------------------------------------ exact facet test
+
+__device__ __forceinline__ int sgn_ll(long long v) { return (v > 0) - (v < 0); }
+
+// sign(d . (a x b)); a, b, d have int32 components below 2^23 in magnitude,
+// so a x b fits int64 (< 2^47) and the dot needs int128 (< 2^72).
+__device__ __forceinline__ int orient_sign(int ax, int ay, int az, int bx, int by, int bz,
+                                           int dx, int dy, int dz)
+{
+    long long cx = (long long)ay * bz - (long long)az * by;
+    long long cy = (long long)az * bx - (long long)ax * bz;
+    long long cz = (long long)ax * by - (long long)ay * bx;
+    __int128 r = (__int128)cx * dx + (__int128)cy * dy + (__int128)cz * dz;
+    return (r > 0) - (r < 0);
+}
+
+// Segment lying in the facet's plane: clip l in [0,1] against the four edge
+// half-planes of the parallelogram, projected along its normal's dominant
+// axis; bounds are kept as exact fractions.  Open segment meets the closed
+// facet iff lo <= hi, lo < 1 and hi > 0.
+static __device__ __noinline__ bool coplanar_hit(const Seg &s, const Leaf &L)
+{
+    int a0 = L.dom == 0 ? 1 : 0;
+    int a1 = L.dom == 2 ? 1 : 2;
+    auto pick = [](int x, int y, int z, int a) { return a == 0 ? x : (a == 1 ? y : z); };
+    long long P0 = pick(s.px, s.py, s.pz, a0), P1 = pick(s.px, s.py, s.pz, a1);
+    long long D0 = pick(s.dx, s.dy, s.dz, a0), D1 = pick(s.dx, s.dy, s.dz, a1);
+    long long O0 = pick(L.ox, L.oy, L.oz, a0), O1 = pick(L.ox, L.oy, L.oz, a1);
+    long long U0 = pick(L.ux, L.uy, L.uz, a0), U1 = pick(L.ux, L.uy, L.uz, a1);
+    long long V0 = pick(L.vx, L.vy, L.vz, a0), V1 = pick(L.vx, L.vy, L.vz, a1);
+    int sig = sgn_ll(U0 * V1 - U1 * V0);      // != 0: the dominant normal component
+    long long cx[4] = {O0, O0 + U0, O0 + U0 + V0, O0 + V0};
+    long long cy[4] = {O1, O1 + U1, O1 + U1 + V1, O1 + V1};
+    long long ex[4] = {U0, V0, -U0, -V0};
+    long long ey[4] = {U1, V1, -U1, -V1};
+    long long lon = 0, lod = 1, hin = 1, hid = 1;
+    for (int k = 0; k < 4; k++) {
+        long long al = sig * (ex[k] * (P1 - cy[k]) - ey[k] * (P0 - cx[k]));
+        long long be = sig * (ex[k] * D1 - ey[k] * D0);
+        if (be > 0) {            // l >= -al / be
+            if ((__int128)(-al) * lod > (__int128)lon * be) { lon = -al; lod = be; }
+        } else if (be < 0) {     // l <= al / (-be)
+            if ((__int128)al * hid < (__int128)hin * (-be)) { hin = al; hid = -be; }
+        } else if (al < 0) {
+            return false;
+        }
+    }
+    return ((__int128)lon * hid <= (__int128)hin * lod) && (lon < lod) && (hin > 0);
+}
+
+// Exact: does the open segment s meet the closed facet L?
+__device__ __forceinline__ bool facet_hit_exact(const Seg &s, const Leaf &L)
+{
+    long long rx = s.px - L.ox, ry = s.py - L.oy, rz = s.pz - L.oz;
+    long long sp = (long long)L.nx * rx + (long long)L.ny * ry + (long long)L.nz * rz;
+    long long sd = (long long)L.nx * s.dx + (long long)L.ny * s.dy + (long long)L.nz * s.dz;
+    int a = sgn_ll(sp), b = sgn_ll(sp + sd);
+    if (a == b) return a == 0 ? coplanar_hit(s, L) : false;
+    if (a == 0 || b == 0) return false;      // touches the plane only at an endpoint
+    // corners relative to P, in cyclic order O, O+U, O+U+V, O+V
+    int c0x = L.ox - s.px, c0y = L.oy - s.py, c0z = L.oz - s.pz;
+    int c1x = c0x + L.ux, c1y = c0y + L.uy, c1z = c0z + L.uz;
+    int c2x = c1x + L.vx, c2y = c1y + L.vy, c2z = c1z + L.vz;
+    int c3x = c0x + L.vx, c3y = c0y + L.vy, c3z = c0z + L.vz;
+    int e0 = orient_sign(c0x, c0y, c0z, c1x, c1y, c1z, s.dx, s.dy, s.dz);
+    int e1 = orient_sign(c1x, c1y, c1z, c2x, c2y, c2z, s.dx, s.dy, s.dz);
+    int e2 = orient_sign(c2x, c2y, c2z, c3x, c3y, c3z, s.dx, s.dy, s.dz);
+    int e3 = orient_sign(c3x, c3y, c3z, c0x, c0y, c0z, s.dx, s.dy, s.dz);
+    bool nonneg = (e0 >= 0) & (e1 >= 0) & (e2 >= 0) & (e3 >= 0);
+    bool nonpos = (e0 <= 0) & (e1 <= 0) & (e2 <= 0) & (e3 <= 0);
+    return nonneg | nonpos;
+}
+
+// Strict facing test: (u x v) . (x - O) > 0, exact in int64 (|n| < 2^31).
+__device__ __forceinline__ bool front_of(const Leaf &L, int x, int y, int z)
+{
+    long long v = (long long)L.nx * (x - L.ox) + (long long)L.ny * (y - L.oy) +
+                  (long long)L.nz * (z - L.oz);
+    return v > 0;
+}
+
+__device__ __forceinline__ Leaf load_leaf(const Leaf *leaves, int g)
+{
+    const int4 *p = reinterpret_cast<const int4 *>(leaves + g);
+    int4 a = __ldg(p), b = __ldg(p + 1), c = __ldg(p + 2), d = __ldg(p + 3);
+    Leaf L;
+    L.ox = a.x; L.oy = a.y; L.oz = a.z; L.building = a.w;
+    L.ux = b.x; L.uy = b.y; L.uz = b.z; L.scene = b.w;
+    L.vx = c.x; L.vy = c.y; L.vz = c.z; L.dom = c.w;
+    L.nx = d.x; L.ny = d.y; L.nz = d.z; L.pad = d.w;
+    return L;
+}
+
+// ------------------------------------------------------------ packet walk
+
+// Per-lane test counts; summed over the warp once per task (flush_counters).
+struct WalkCounters {
+    unsigned long long node_tests = 0, leaf_tests = 0, undecided = 0, exact = 0, segments = 0;
+};
+
+__device__ __forceinline__ unsigned long long warp_sum(unsigned long long v)
+{
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    return v;
+}
+
+__device__ __forceinline__ void flush_counters(WalkCounters &wc, unsigned long long *ctr)
+{
+    unsigned long long a = warp_sum(wc.node_tests), b = warp_sum(wc.leaf_tests),
+                       c = warp_sum(wc.undecided), d = warp_sum(wc.exact),
+                       e = warp_sum(wc.segments);
+    if ((threadIdx.x & 31) == 0) {
+        if (a) atomicAdd(ctr + C_NODE_TESTS, a);
+        if (b) atomicAdd(ctr + C_LEAF_TESTS, b);
+        if (c) atomicAdd(ctr + C_UNDECIDED, c);
+        if (d) atomicAdd(ctr + C_EXACT_TESTS, d);
+        if (e) atomicAdd(ctr + C_SEGMENTS, e);
+    }
+    wc = WalkCounters();
+}
+
+// Walks the BVH for the packet.  Must be called by all 32 lanes with the
+// same `alive` (lanes whose segment takes part).  Returns the lanes whose
+// segment no facet blocks.  LeafFn(seg, leaf, counters) -> bool hit.
+// (dirx, diry, dirz) is a packet direction used to visit the nearer child
+// first.  `budget` bounds the number of steps (a valid tree needs at most
+// 2 * nodes + 2); when it runs out, IVM_ERR_TIMEOUT is raised.
+template <class LeafFn>
+__device__ __forceinline__ unsigned walk_packet(const Seg &s, unsigned alive, const Node *nodes,
+                                                const Leaf *leaves, int root, float dirx,
+                                                float diry, float dirz, int budget, int *err,
+                                                WalkCounters &wc, LeafFn leaf_hit)
+{
+    const int lane = threadIdx.x & 31;
+    int s0 = 0, s1 = 0, sp = 0;   // stack: entry k lives in lane k&31 of s0 / s1
+    int node = root;
+    while (alive) {
+        if (--budget < 0) {
+            if (lane == 0) raise_error(err, IVM_ERR_TIMEOUT);
+            return 0;
+        }
+        bool have_next = false;
+        if (node < 0) {
+            const Leaf L = load_leaf(leaves, ~node);
+            bool me = (alive >> lane) & 1u;
+            bool hit = me && leaf_hit(s, L, wc);
+            wc.leaf_tests += me;
+            alive &= ~__ballot_sync(kFull, hit);
+        } else {
+            const float4 *np = reinterpret_cast<const float4 *>(nodes + node);
+            float4 A = __ldg(np), B = __ldg(np + 1), C = __ldg(np + 2);
+            int4 D = __ldg(reinterpret_cast<const int4 *>(np + 3));
+            bool me = (alive >> lane) & 1u;
+            bool hl = me && seg_box(s, A.x, A.y, A.z, A.w, B.x, B.y);
+            bool hr = me && seg_box(s, B.z, B.w, C.x, C.y, C.z, C.w);
+            wc.node_tests += 2 * me;
+            unsigned ml = __ballot_sync(kFull, hl), mr = __ballot_sync(kFull, hr);
+            if (ml && mr) {
+                // nearer child first along the packet direction
+                float kl = (A.x + A.w) * dirx + (A.y + B.x) * diry + (A.z + B.y) * dirz;
+                float kr = (B.z + C.y) * dirx + (B.w + C.z) * diry + (C.x + C.w) * dirz;
+                int first = kl <= kr ? D.x : D.y, second = kl <= kr ? D.y : D.x;
+                if (sp >= kStackDepth) {
+                    if (lane == 0) raise_error(err, IVM_ERR_INTERNAL);
+                    return 0;
+                }
+                if (lane == (sp & 31)) {
+                    if (sp < 32) s0 = second; else s1 = second;
+                }
+                sp++;
+                node = first;
+                have_next = true;
+            } else if (ml) {
+                node = D.x;
+                have_next = true;
+            } else if (mr) {
+                node = D.y;
+                have_next = true;
+            }
+        }
+        if (!have_next) {
+            if (sp == 0) break;
+            sp--;
+            int v0 = __shfl_sync(kFull, s0, sp & 31), v1 = __shfl_sync(kFull, s1, sp & 31);
+            node = sp < 32 ? v0 : v1;
+        }
+    }
+    return alive;
+}
+
+struct ExactLeaf {
+    __device__ __forceinline__ bool operator()(const Seg &s, const Leaf &L, WalkCounters &wc) const
+    {
+        wc.exact++;
+        return facet_hit_exact(s, L);
+    }
+};
+
+}  // namespace ivm

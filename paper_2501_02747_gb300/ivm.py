@@ -1,0 +1,269 @@
+"""Python binding of libivm.so (include/ivm.h): argument marshalling only.
+
+Every step of the computation runs in the CUDA library; this module turns
+numpy arrays / torch tensors into the C structs and pointers the ABI takes,
+allocates outputs with torch on the context's device when the caller gives
+none, and raises ``IvmError`` on a non-zero return code.  There is no
+fallback: if the library is not built or cannot be loaded, ``lib()`` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+IVM_OK, IVM_ERR_ARG, IVM_ERR_RANGE, IVM_ERR_CAPACITY = 0, 1, 2, 3
+IVM_ERR_TIMEOUT, IVM_ERR_CUDA, IVM_ERR_INTERNAL = 4, 5, 6
+IVM_MODE_EXACT, IVM_MODE_FILTERED, IVM_MODE_LEARNED = 0, 1, 2
+IVM_FLAG_PERSISTENT, IVM_FLAG_GRAPH = 1, 2
+
+
+class ivm_facet(ctypes.Structure):
+    _fields_ = [("o", ctypes.c_int32 * 3), ("u", ctypes.c_int32 * 3), ("v", ctypes.c_int32 * 3),
+                ("building", ctypes.c_int32)]
+
+
+class ivm_scene(ctypes.Structure):
+    _fields_ = [("facets", ctypes.c_void_p), ("n_facets", ctypes.c_int32)]
+
+
+class ivm_params(ctypes.Structure):
+    _fields_ = [("samples_per_side", ctypes.c_int32), ("max_order", ctypes.c_int32),
+                ("mode", ctypes.c_int32), ("tile", ctypes.c_int32),
+                ("warps_per_block", ctypes.c_int32), ("flags", ctypes.c_int32)]
+
+
+class ivm_stats(ctypes.Structure):
+    _fields_ = [("pairs", ctypes.c_uint64), ("cand_pairs", ctypes.c_uint64),
+                ("segments", ctypes.c_uint64), ("node_tests", ctypes.c_uint64),
+                ("leaf_tests", ctypes.c_uint64), ("undecided", ctypes.c_uint64),
+                ("exact_tests", ctypes.c_uint64), ("ranker_hits", ctypes.c_uint64),
+                ("ms_ingest", ctypes.c_float), ("ms_bvh", ctypes.c_float),
+                ("ms_screen", ctypes.c_float), ("ms_traverse", ctypes.c_float),
+                ("ms_tree", ctypes.c_float), ("ms_total", ctypes.c_float)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class ivm_tree_summary(ctypes.Structure):
+    _fields_ = [("count", ctypes.c_uint64), ("fp0", ctypes.c_uint64), ("fp1", ctypes.c_uint64)]
+
+
+_VP = ctypes.c_void_p
+_lib = None
+
+# Every function include/ivm.h declares, with its ctypes signature.
+SIGNATURES = {
+    "ivm_create": ([ctypes.POINTER(_VP), ctypes.c_int, _VP], ctypes.c_int),
+    "ivm_destroy": ([_VP], ctypes.c_int),
+    "ivm_build_matrix": ([_VP, ctypes.POINTER(ivm_scene), ctypes.c_int32,
+                          ctypes.POINTER(ivm_params), ctypes.POINTER(_VP),
+                          ctypes.POINTER(ivm_stats)], ctypes.c_int),
+    "ivm_build_table": ([_VP, ctypes.POINTER(ivm_scene), ctypes.c_int32,
+                         ctypes.POINTER(ivm_params), ctypes.POINTER(_VP), ctypes.POINTER(_VP),
+                         ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(_VP),
+                         ctypes.POINTER(_VP), ctypes.POINTER(ivm_stats)], ctypes.c_int),
+    "ivm_expand_image_tree": ([_VP, _VP, _VP, _VP, ctypes.c_int32, ctypes.c_int64,
+                               ctypes.c_int32, _VP, _VP, ctypes.c_int64,
+                               ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
+    "ivm_strerror": ([ctypes.c_int], ctypes.c_char_p),
+    "ivm_kernel_launches": ([], ctypes.c_uint64),
+}
+
+
+def kernel_launches() -> int:
+    return int(lib().ivm_kernel_launches())
+
+
+class IvmError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        super().__init__(f"{where}: {lib().ivm_strerror(code).decode()} (code {code})")
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Load libivm.so (build it first with paper_2501_02747_gb300.build.build())."""
+    global _lib
+    if _lib is None:
+        path = lib_path()
+        if not os.path.exists(path):
+            raise RuntimeError(f"libivm.so is not built ({path}); run "
+                               "paper_2501_02747_gb300.build.build() first")
+        L = ctypes.CDLL(path)
+        for name, (args, res) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = L
+    return _lib
+
+
+def _check(code, where):
+    if code != IVM_OK:
+        raise IvmError(code, where)
+
+
+def _addr(x):
+    """Data pointer of a torch tensor or numpy array (must be contiguous)."""
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return x.data_ptr()
+    if not x.flags["C_CONTIGUOUS"]:
+        raise ValueError("array must be C-contiguous")
+    return x.ctypes.data
+
+
+def words(n: int) -> int:
+    return (n + 31) // 32
+
+
+class Context:
+    """An ivm context on one device and one CUDA stream."""
+
+    def __init__(self, device: int = 0, stream=None):
+        import torch
+        self.device = device
+        if stream is None:
+            stream = torch.cuda.current_stream(device)
+        self.stream = stream
+        h = _VP()
+        _check(lib().ivm_create(ctypes.byref(h), device, _VP(stream.cuda_stream)), "ivm_create")
+        self.handle = h
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().ivm_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def _params(s, K=0, mode=IVM_MODE_EXACT, tile=0, warps_per_block=0, flags=0):
+    return ivm_params(s, K, mode, tile, warps_per_block, flags)
+
+
+def _scenes(facet_list):
+    arr = (ivm_scene * len(facet_list))()
+    keep = []
+    for k, f in enumerate(facet_list):
+        if hasattr(f, "data_ptr"):
+            keep.append(f)
+            arr[k].facets = f.data_ptr()
+            arr[k].n_facets = f.shape[0]
+        else:
+            a = np.ascontiguousarray(f, dtype=np.int32).reshape(-1, 10)
+            keep.append(a)
+            arr[k].facets = a.ctypes.data
+            arr[k].n_facets = a.shape[0]
+    return arr, keep
+
+
+def ivm_build_matrix(ctx, facets, s, mode=IVM_MODE_EXACT, flags=0, tile=0, warps_per_block=0,
+                     out=None):
+    """Matrix of one scene (facets int32 [N][10]) or a list of scenes.
+
+    Returns uint32 torch tensors [N][W] on the context's device (or the given
+    `out` buffers, host or device) and an ivm_stats."""
+    import torch
+    single = not isinstance(facets, (list, tuple))
+    flist = [facets] if single else list(facets)
+    scenes, keep = _scenes(flist)
+    if out is None:
+        out = [torch.empty((f.shape[0], words(f.shape[0])), dtype=torch.int32,
+                           device=f"cuda:{ctx.device}") for f in flist]
+    elif single:
+        out = [out]
+    ptrs = (_VP * len(out))(*[_addr(o) for o in out])
+    st = ivm_stats()
+    p = _params(s, 0, mode, tile, warps_per_block, flags)
+    _check(lib().ivm_build_matrix(ctx.handle, scenes, len(flist), ctypes.byref(p), ptrs,
+                                  ctypes.byref(st)), "ivm_build_matrix")
+    return (out[0] if single else out), st
+
+
+def ivm_build_table(ctx, facets, s, tx, rx, mode=IVM_MODE_EXACT, flags=0, tile=0,
+                    warps_per_block=0, out=None):
+    """Table of one scene or a list of scenes: (table [S][2][W], los [S]) per scene."""
+    import torch
+    single = not isinstance(facets, (list, tuple))
+    flist = [facets] if single else list(facets)
+    txs = [tx] if single else list(tx)
+    rxs = [rx] if single else list(rx)
+    scenes, keep = _scenes(flist)
+    keep_pos = []
+
+    def pos(a):
+        if hasattr(a, "data_ptr"):
+            return a
+        b = np.ascontiguousarray(a, dtype=np.int32).reshape(-1, 3)
+        keep_pos.append(b)
+        return b
+
+    txs = [pos(a) for a in txs]
+    rxs = [pos(a) for a in rxs]
+    n_snap = (ctypes.c_int64 * len(flist))(*[int(a.shape[0]) for a in txs])
+    if out is None:
+        dev = f"cuda:{ctx.device}"
+        out = [(torch.empty((int(t.shape[0]), 2, words(f.shape[0])), dtype=torch.int32, device=dev),
+                torch.empty((int(t.shape[0]),), dtype=torch.uint8, device=dev))
+               for f, t in zip(flist, txs)]
+    elif single:
+        out = [out]
+    tab_p = (_VP * len(out))(*[_addr(o[0]) for o in out])
+    los_p = (_VP * len(out))(*[_addr(o[1]) for o in out])
+    tx_p = (_VP * len(out))(*[_addr(a) for a in txs])
+    rx_p = (_VP * len(out))(*[_addr(a) for a in rxs])
+    st = ivm_stats()
+    p = _params(s, 0, mode, tile, warps_per_block, flags)
+    _check(lib().ivm_build_table(ctx.handle, scenes, len(flist), ctypes.byref(p), tx_p, rx_p,
+                                 n_snap, tab_p, los_p, ctypes.byref(st)), "ivm_build_table")
+    return (out[0] if single else out), st
+
+
+def ivm_expand_image_tree(ctx, matrix, table, los, n_facets, max_order, paths_capacity=None,
+                          summary=None, paths=None):
+    """Summaries uint64 [S][K+1][3] (torch, on device unless `summary` is given);
+    with paths_capacity, also the path records int32 [n][K+2] and the total."""
+    import torch
+    S = int(table.shape[0])
+    K = int(max_order)
+    if summary is None:
+        summary = torch.empty((S, K + 1, 3), dtype=torch.int64, device=f"cuda:{ctx.device}")
+    total = ctypes.c_int64(0)
+    cap = 0
+    if paths_capacity is not None:
+        cap = int(paths_capacity)
+        if paths is None:
+            paths = torch.empty((max(cap, 1), K + 2), dtype=torch.int32,
+                                device=f"cuda:{ctx.device}")
+    code = lib().ivm_expand_image_tree(ctx.handle, _addr(matrix), _addr(table), _addr(los),
+                                       int(n_facets), S, K, _addr(summary),
+                                       _addr(paths) if paths_capacity is not None else None,
+                                       cap, ctypes.byref(total))
+    if code == IVM_ERR_CAPACITY:
+        return summary, paths, int(total.value), code
+    _check(code, "ivm_expand_image_tree")
+    if paths_capacity is not None:
+        return summary, paths[:min(cap, total.value)], int(total.value), code
+    return summary, int(total.value)

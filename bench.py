@@ -23,7 +23,6 @@ host cores instead.
 from __future__ import annotations
 
 import argparse
-import hashlib
 import json
 import os
 import statistics
@@ -228,7 +227,9 @@ def run_ours(args, ws, rank, local):
 
     forms = {
         "plain": dict(mode=ivm.IVM_MODE_EXACT, flags=0),
-        "fast": dict(mode=ivm.IVM_MODE_FILTERED, flags=ivm.IVM_FLAG_PERSISTENT),
+        "fast": dict(mode=ivm.IVM_MODE_FILTERED,
+                     flags=ivm.IVM_FLAG_PERSISTENT | ivm.IVM_FLAG_OCCLUDER_CACHE
+                     | ivm.IVM_FLAG_DEDUP_SOURCES),
     }
 
     def step(form, fac, tx, rx, M, T, L, summ):
@@ -289,7 +290,8 @@ def run_ours(args, ws, rank, local):
         "scaling": "weak", "vs_baseline": None, "dtype": "int64/int128 + fp32 filter",
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "form": "fast: FP32 filter + exact fallback, "
-                   "persistent work queue", "l2": "flushed between steps (512 MB write)",
+                   "persistent work queue, occluder cache, one row per run of equal "
+                   "source positions", "l2": "flushed between steps (512 MB write)",
                    "facets": N, "snapshots": S, "samples_per_side": s, "max_order": K,
                    "pair_tests_per_step": units},
         "snapshot_tables_per_s": ws * S / (ms_fast / 1e3),

@@ -76,6 +76,8 @@ extern "C" {
 /* ------------------------------------------------------------ flag bits */
 #define IVM_FLAG_PERSISTENT 1  /* persistent kernels over a work queue */
 #define IVM_FLAG_GRAPH 2       /* replay the call's launches as a CUDA graph */
+#define IVM_FLAG_OCCLUDER_CACHE 4 /* test each warp's last blockers before the BVH */
+#define IVM_FLAG_DEDUP_SOURCES 8  /* table: trace one row per run of equal positions */
 
 typedef struct ivm_facet {
     int32_t o[3], u[3], v[3]; /* cm; u x v points outward */
@@ -106,6 +108,8 @@ typedef struct ivm_stats {
     uint64_t exact_tests;     /* facet tests decided by integer arithmetic */
     uint64_t ranker_hits;     /* blocked segments whose occluder lay in the
                                  ranker's first proposed cluster (LEARNED) */
+    uint64_t cache_hits;      /* segments blocked by an occluder-cache facet */
+    uint64_t dedup_rows;      /* table rows copied from an equal-position row */
     float ms_ingest, ms_bvh, ms_screen, ms_traverse, ms_tree, ms_total;
 } ivm_stats;
 

@@ -158,9 +158,13 @@ __global__ void k_refit(DevScenes g)
 {
     int f = blockIdx.x * blockDim.x + threadIdx.x;
     if (f >= g.total_facets) return;
+    // boxes are stored enlarged by half a unit (see seg_box in traverse.cuh)
     float bx[6];
     const int *b = g.box + 6 * (size_t)f;
-    for (int a = 0; a < 6; a++) bx[a] = (float)b[a];
+    for (int a = 0; a < 3; a++) {
+        bx[a] = (float)b[a] - 0.5f;
+        bx[3 + a] = (float)b[3 + a] + 0.5f;
+    }
     int ps = g.parent[f];
     int guard = 0;
     while (ps >= 0 && guard++ < 128) {

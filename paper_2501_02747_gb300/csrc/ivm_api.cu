@@ -18,7 +18,7 @@ namespace {
 
 enum Slot {
     S_FACETS, S_DESC, S_LEAF, S_FSCENE, S_BOX, S_SX, S_SY, S_SZ, S_KEYS, S_SORTED, S_BOUNDS,
-    S_ORDER, S_NODES, S_PARENT, S_VISITS, S_PAIRS, S_OUT, S_TX, S_RX, S_LOS,
+    S_ORDER, S_NODES, S_PARENT, S_VISITS, S_PAIRS, S_OUT, S_TX, S_RX, S_LOS, S_REP,
     S_T_MAT, S_T_TAB, S_T_LOS, S_T_SUM, S_T_DEG, S_T_ROW, S_T_COL, S_T_WT, S_T_XA, S_T_XB,
     S_T_CNT, S_T_OFF, S_T_BS, S_T_BO, S_T_PATHS,
     S_COUNT
@@ -118,6 +118,8 @@ LaunchCfg launch_cfg(const ivm_ctx *c, const ivm_params *p)
     L.warps_per_block = p->warps_per_block > 0 ? p->warps_per_block : 4;
     L.tile = p->tile > 0 ? p->tile : (L.persistent ? 4 : 1);
     L.n_sm = c->n_sm;
+    L.cache = (p->flags & IVM_FLAG_OCCLUDER_CACHE) != 0;
+    L.dedup = (p->flags & IVM_FLAG_DEDUP_SOURCES) != 0;
     return L;
 }
 
@@ -241,6 +243,8 @@ int fill_stats(ivm_ctx *c, ivm_stats *st, unsigned long long pairs, int phases)
     st->undecided = c->h_ctr[C_UNDECIDED];
     st->exact_tests = c->h_ctr[C_EXACT_TESTS];
     st->ranker_hits = c->h_ctr[C_RANKER_HITS];
+    st->cache_hits = c->h_ctr[C_CACHE_HITS];
+    st->dedup_rows = c->h_ctr[C_DEDUP_ROWS];
     st->ms_ingest = elapsed(c->ev[0], c->ev[1]);
     st->ms_bvh = elapsed(c->ev[1], c->ev[2]);
     if (phases >= 3) st->ms_screen = elapsed(c->ev[2], c->ev[3]);
@@ -443,7 +447,9 @@ extern "C" int ivm_build_table(ivm_ctx *c, const ivm_scene *scenes, int32_t n_sc
     CK(cudaEventRecord(c->ev[0], c->stream));
     if ((r = build_geometry(c, g))) return r;
     const LaunchCfg cfg = launch_cfg(c, params);
-    CK(launch_table(g, snaps, chunks, cfg, c->d_misc + 2, c->d_ctr, c->d_err, c->stream));
+    if (cfg.dedup && (r = ensure(c, S_REP, sizeof(int) * 2 * (size_t)snaps))) return r;
+    CK(launch_table(g, snaps, chunks, cfg, ptr<int>(c, S_REP), c->d_misc + 2, c->d_ctr, c->d_err,
+                    c->stream));
     CK(cudaEventRecord(c->ev[4], c->stream));
     if ((r = read_error(c))) return r;
     for (int k = 0; k < n_scenes; k++) {

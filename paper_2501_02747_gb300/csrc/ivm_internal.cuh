@@ -69,6 +69,8 @@ enum Counter {
     C_EXACT_TESTS,
     C_RANKER_HITS,
     C_CAND_PAIRS,
+    C_CACHE_HITS,
+    C_DEDUP_ROWS,
     C_COUNT_
 };
 
@@ -114,13 +116,15 @@ struct LaunchCfg {
     int warps_per_block;  // 1..16
     int tile;             // work items taken per queue pop (persistent)
     int n_sm;
+    int cache;            // occluder cache in front of the BVH walk
+    int dedup;            // table: compute one row per run of equal source positions
 };
 
 cudaError_t launch_matrix(const DevScenes &g, const int2 *pairs, unsigned long long npairs,
                           const LaunchCfg &cfg, unsigned long long *work,
                           unsigned long long *ctr, int *err, cudaStream_t st);
 cudaError_t launch_table(const DevScenes &g, long long total_snap, long long total_los_chunks,
-                         const LaunchCfg &cfg, unsigned long long *work,
+                         const LaunchCfg &cfg, int *rep, unsigned long long *work,
                          unsigned long long *ctr, int *err, cudaStream_t st);
 
 }  // namespace ivm

@@ -16,13 +16,14 @@
 
 namespace ivm {
 
-template <class LeafFn>
+template <bool CACHE, class LeafFn>
 __device__ __forceinline__ void decide_pair(const DevScenes &g, int gi, int gj, int *err,
-                                            WalkCounters &wc, LeafFn leaf)
+                                            WalkCounters &wc, LeafFn leaf, OccluderCache &cache)
 {
     const int lane = threadIdx.x & 31;
     const Leaf Li = load_leaf(g.leaf, gi), Lj = load_leaf(g.leaf, gj);
     const SceneDesc &D = g.desc[Li.scene];
+    if (CACHE) cache.enter_scene(Li.scene);
     const int s = D.s, s2 = s * s, total = s2 * s2;
     const int i = gi - D.facet0, j = gj - D.facet0;
     const int baseI = D.sample0 + i * s2, baseJ = D.sample0 + j * s2;
@@ -45,8 +46,8 @@ __device__ __forceinline__ void decide_pair(const DevScenes &g, int gi, int gj, 
         if (!alive) continue;
         wc.segments += face;
         const Seg sg = make_seg(px, py, pz, qx, qy, qz);
-        alive = walk_packet(sg, alive, g.nodes, g.leaf, D.root, dirx, diry, dirz, budget, err,
-                            wc, leaf);
+        alive = occlude<CACHE>(sg, alive, g.nodes, g.leaf, D.root, dirx, diry, dirz, budget, err,
+                               wc, leaf, cache);
         if (alive) {
             visible = true;
             break;
@@ -58,18 +59,19 @@ __device__ __forceinline__ void decide_pair(const DevScenes &g, int gi, int gj, 
     }
 }
 
-template <bool PERSIST, class LeafFn>
+template <bool PERSIST, bool CACHE, class LeafFn>
 __global__ void k_matrix(DevScenes g, const int2 *pairs, unsigned long long npairs, int tile,
                          unsigned long long *work, unsigned long long *ctr, int *err)
 {
     WalkCounters wc;
     LeafFn leaf;
+    OccluderCache cache;
     const int lane = threadIdx.x & 31;
     if (!PERSIST) {
         unsigned long long w = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
         if (w < npairs) {
             const int2 p = pairs[w];
-            decide_pair(g, p.x, p.y, err, wc, leaf);
+            decide_pair<CACHE>(g, p.x, p.y, err, wc, leaf, cache);
         }
     } else {
         for (;;) {
@@ -80,43 +82,55 @@ __global__ void k_matrix(DevScenes g, const int2 *pairs, unsigned long long npai
             unsigned long long end = min(base + (unsigned long long)tile, npairs);
             for (unsigned long long w = base; w < end; w++) {
                 const int2 p = pairs[w];
-                decide_pair(g, p.x, p.y, err, wc, leaf);
+                decide_pair<CACHE>(g, p.x, p.y, err, wc, leaf, cache);
             }
         }
     }
     flush_counters(wc, ctr);
 }
 
-template <class LeafFn>
-static cudaError_t launch_matrix_t(const DevScenes &g, const int2 *pairs,
-                                   unsigned long long npairs, const LaunchCfg &cfg,
-                                   unsigned long long *work, unsigned long long *ctr, int *err,
-                                   cudaStream_t st)
+template <bool PERSIST, bool CACHE, class LeafFn>
+static void launch_one(const DevScenes &g, const int2 *pairs, unsigned long long npairs,
+                       const LaunchCfg &cfg, unsigned long long *work, unsigned long long *ctr,
+                       int *err, cudaStream_t st)
 {
     const int threads = 32 * cfg.warps_per_block;
-    if (npairs == 0) return cudaSuccess;
-    if (cfg.persistent) {
+    auto kern = k_matrix<PERSIST, CACHE, LeafFn>;
+    if (PERSIST) {
         int per_sm = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_matrix<true, LeafFn>, threads, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, 0);
         int blocks = cfg.n_sm * (per_sm > 0 ? per_sm : 1);
         cudaMemsetAsync(work, 0, sizeof(unsigned long long), st);
-        k_matrix<true, LeafFn><<<blocks, threads, 0, st>>>(g, pairs, npairs, cfg.tile, work, ctr, err);
+        kern<<<blocks, threads, 0, st>>>(g, pairs, npairs, cfg.tile, work, ctr, err);
     } else {
         unsigned long long blocks = (npairs + cfg.warps_per_block - 1) / cfg.warps_per_block;
-        k_matrix<false, LeafFn><<<(unsigned)blocks, threads, 0, st>>>(g, pairs, npairs, 1, work, ctr,
-                                                                     err);
+        kern<<<(unsigned)blocks, threads, 0, st>>>(g, pairs, npairs, 1, work, ctr, err);
     }
-    note_launches(1);
-    return cudaGetLastError();
+}
+
+template <class LeafFn>
+static void launch_leaf(const DevScenes &g, const int2 *pairs, unsigned long long npairs,
+                        const LaunchCfg &cfg, unsigned long long *work, unsigned long long *ctr,
+                        int *err, cudaStream_t st)
+{
+    if (cfg.persistent) {
+        if (cfg.cache) launch_one<true, true, LeafFn>(g, pairs, npairs, cfg, work, ctr, err, st);
+        else launch_one<true, false, LeafFn>(g, pairs, npairs, cfg, work, ctr, err, st);
+    } else {
+        if (cfg.cache) launch_one<false, true, LeafFn>(g, pairs, npairs, cfg, work, ctr, err, st);
+        else launch_one<false, false, LeafFn>(g, pairs, npairs, cfg, work, ctr, err, st);
+    }
 }
 
 cudaError_t launch_matrix(const DevScenes &g, const int2 *pairs, unsigned long long npairs,
                           const LaunchCfg &cfg, unsigned long long *work,
                           unsigned long long *ctr, int *err, cudaStream_t st)
 {
-    if (cfg.mode == IVM_MODE_EXACT)
-        return launch_matrix_t<ExactLeaf>(g, pairs, npairs, cfg, work, ctr, err, st);
-    return launch_matrix_t<FilteredLeaf>(g, pairs, npairs, cfg, work, ctr, err, st);
+    if (npairs == 0) return cudaSuccess;
+    if (cfg.mode == IVM_MODE_EXACT) launch_leaf<ExactLeaf>(g, pairs, npairs, cfg, work, ctr, err, st);
+    else launch_leaf<FilteredLeaf>(g, pairs, npairs, cfg, work, ctr, err, st);
+    note_launches(1);
+    return cudaGetLastError();
 }
 
 }  // namespace ivm

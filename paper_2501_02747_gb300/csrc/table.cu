@@ -11,6 +11,10 @@
 // time: with s*s <= 32 samples, floor(32 / (s*s)) facets share a packet; with
 // more samples a facet takes several packets and stops at the first free one.
 // Each 32-facet word of the row is written once, by lane 0.
+//
+// Runs of equal positions (a static Tx, a receiver that pauses) have equal
+// rows: with deduplication on, a pre-pass finds the first snapshot of each
+// run, only that row is traced, and a post-pass copies it over the run.
 #include "ivm_internal.cuh"
 #include "traverse.cuh"
 #include "filter.cuh"
@@ -43,9 +47,10 @@ __device__ __forceinline__ bool in_range(long long x, long long y, long long z)
            (z > -kCoordLimit) & (z < kCoordLimit);
 }
 
-template <class LeafFn>
-__device__ __forceinline__ void table_item(const DevScenes &g, long long item, int *err,
-                                           WalkCounters &wc, LeafFn leaf)
+template <bool CACHE, class LeafFn>
+__device__ __forceinline__ void table_item(const DevScenes &g, long long item, const int *rep,
+                                           int *err, WalkCounters &wc, LeafFn leaf,
+                                           OccluderCache &cache)
 {
     const int lane = threadIdx.x & 31;
     const long long T = item >> 1;
@@ -53,6 +58,8 @@ __device__ __forceinline__ void table_item(const DevScenes &g, long long item, i
     const int sc = scene_of_snap(g.desc, g.n_scenes, T);
     const SceneDesc &D = g.desc[sc];
     const long long t = T - D.snap0;
+    if (rep && rep[item] != t) return;          // a copy of its run's first row
+    if (CACHE) cache.enter_scene(sc);
     const int *src = (side ? D.rx : D.tx) + 3 * t;
     const long long k = 2LL * D.s;
     const long long X0 = k * src[0], X1 = k * src[1], X2 = k * src[2];
@@ -80,20 +87,19 @@ __device__ __forceinline__ void table_item(const DevScenes &g, long long item, i
                 unsigned m = fm;
                 for (int q = 0; q < gi && q < 31; q++) m &= m - 1;
                 const int jbit = mine ? __ffs(m) - 1 : 0;
-                const int gf = D.facet0 + 32 * c + jbit;
                 const int sidx = D.sample0 + (32 * c + jbit) * s2 + b;
                 int qx = 0, qy = 0, qz = 0;
                 if (mine) { qx = __ldg(g.sx + sidx); qy = __ldg(g.sy + sidx); qz = __ldg(g.sz + sidx); }
                 unsigned alive = __ballot_sync(kFull, mine);
-                const int lead = __shfl_sync(kFull, gf, 0);
+                const int lead = D.facet0 + 32 * c + __shfl_sync(kFull, jbit, 0);
                 const Leaf Lf = load_leaf(g.leaf, lead);
                 const float dirx = (float)(2 * Lf.ox + Lf.ux + Lf.vx - 2 * x);
                 const float diry = (float)(2 * Lf.oy + Lf.uy + Lf.vy - 2 * y);
                 const float dirz = (float)(2 * Lf.oz + Lf.uz + Lf.vz - 2 * z);
                 wc.segments += mine;
                 const Seg sg = make_seg(x, y, z, qx, qy, qz);
-                alive = walk_packet(sg, alive, g.nodes, g.leaf, D.root, dirx, diry, dirz, budget,
-                                    err, wc, leaf);
+                alive = occlude<CACHE>(sg, alive, g.nodes, g.leaf, D.root, dirx, diry, dirz,
+                                       budget, err, wc, leaf, cache);
                 const unsigned smask = (s2 == 32) ? kFull : ((1u << s2) - 1u);
                 const bool gvis = mine && ((alive >> (gi * s2)) & smask) != 0u;
                 const unsigned bitv = (gvis && b == 0) ? (1u << jbit) : 0u;
@@ -116,8 +122,8 @@ __device__ __forceinline__ void table_item(const DevScenes &g, long long item, i
                     unsigned alive = __ballot_sync(kFull, mine);
                     wc.segments += mine;
                     const Seg sg = make_seg(x, y, z, qx, qy, qz);
-                    alive = walk_packet(sg, alive, g.nodes, g.leaf, D.root, dirx, diry, dirz,
-                                        budget, err, wc, leaf);
+                    alive = occlude<CACHE>(sg, alive, g.nodes, g.leaf, D.root, dirx, diry, dirz,
+                                           budget, err, wc, leaf, cache);
                     if (alive) {
                         word |= 1u << jbit;
                         break;
@@ -129,13 +135,14 @@ __device__ __forceinline__ void table_item(const DevScenes &g, long long item, i
     }
 }
 
-template <class LeafFn>
+template <bool CACHE, class LeafFn>
 __device__ __forceinline__ void los_item(const DevScenes &g, long long chunk, int *err,
-                                         WalkCounters &wc, LeafFn leaf)
+                                         WalkCounters &wc, LeafFn leaf, OccluderCache &cache)
 {
     const int lane = threadIdx.x & 31;
     const int sc = scene_of_los(g.desc, g.n_scenes, chunk);
     const SceneDesc &D = g.desc[sc];
+    if (CACHE) cache.enter_scene(sc);
     const long long t = (chunk - D.los0) * 32 + lane;
     const bool valid = t < D.nsnap;
     const long long k = 2LL * D.s;
@@ -156,23 +163,25 @@ __device__ __forceinline__ void los_item(const DevScenes &g, long long chunk, in
     const float diry = (float)__shfl_sync(kFull, sg.dy, lead);
     const float dirz = (float)__shfl_sync(kFull, sg.dz, lead);
     if (alive)
-        alive = walk_packet(sg, alive, g.nodes, g.leaf, D.root, dirx, diry, dirz, 4 * D.n + 16,
-                            err, wc, leaf);
+        alive = occlude<CACHE>(sg, alive, g.nodes, g.leaf, D.root, dirx, diry, dirz, 4 * D.n + 16,
+                               err, wc, leaf, cache);
     if (valid) D.los[t] = (uint8_t)((ok && same) || ((alive >> lane) & 1u));
 }
 
 // Items [0, 2 * total_snap) are table rows; items after them are LoS chunks.
-template <bool PERSIST, class LeafFn>
+template <bool PERSIST, bool CACHE, class LeafFn>
 __global__ void k_table(DevScenes g, long long total_snap, long long total_items, int tile,
-                        unsigned long long *work, unsigned long long *ctr, int *err)
+                        const int *rep, unsigned long long *work, unsigned long long *ctr,
+                        int *err)
 {
     WalkCounters wc;
     LeafFn leaf;
+    OccluderCache cache;
     const int lane = threadIdx.x & 31;
     const long long rows = 2 * total_snap;
     auto run = [&](long long it) {
-        if (it < rows) table_item(g, it, err, wc, leaf);
-        else los_item(g, it - rows, err, wc, leaf);
+        if (it < rows) table_item<CACHE>(g, it, rep, err, wc, leaf, cache);
+        else los_item<CACHE>(g, it - rows, err, wc, leaf, cache);
     };
     if (!PERSIST) {
         long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -190,37 +199,122 @@ __global__ void k_table(DevScenes g, long long total_snap, long long total_items
     flush_counters(wc, ctr);
 }
 
-template <class LeafFn>
-static cudaError_t launch_table_t(const DevScenes &g, long long total_snap, long long los_chunks,
-                                  const LaunchCfg &cfg, unsigned long long *work,
-                                  unsigned long long *ctr, int *err, cudaStream_t st)
+// ------------------------------------------------------------ deduplication
+
+// One block of 1024 threads per (scene, side): rep[2 T + side] = local index
+// of the first snapshot of the run of equal positions containing t.  Each
+// thread scans a contiguous chunk; a block max-scan joins the chunks.
+__global__ void k_runs(DevScenes g, int *rep)
 {
-    const long long items = 2 * total_snap + los_chunks;
-    if (items == 0) return cudaSuccess;
+    __shared__ long long carry[1024];
+    const SceneDesc D = g.desc[blockIdx.x];
+    const int side = blockIdx.y;
+    const long long S = D.nsnap;
+    if (S == 0) return;
+    const int *X = side ? D.rx : D.tx;
+    const long long per = (S + 1023) / 1024;
+    const long long b = threadIdx.x * per, e = min(b + per, S);
+    long long last = -1;
+    for (long long t = b; t < e; t++) {
+        bool start = t == 0 || X[3 * t] != X[3 * t - 3] || X[3 * t + 1] != X[3 * t - 2] ||
+                     X[3 * t + 2] != X[3 * t - 1];
+        if (start) last = t;
+    }
+    carry[threadIdx.x] = last;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {   // inclusive max-scan of chunk results
+        long long v = threadIdx.x >= o ? carry[threadIdx.x - o] : -1;
+        __syncthreads();
+        if (v > carry[threadIdx.x]) carry[threadIdx.x] = v;
+        __syncthreads();
+    }
+    long long run = threadIdx.x > 0 ? carry[threadIdx.x - 1] : -1;
+    for (long long t = b; t < e; t++) {
+        bool start = t == 0 || X[3 * t] != X[3 * t - 3] || X[3 * t + 1] != X[3 * t - 2] ||
+                     X[3 * t + 2] != X[3 * t - 1];
+        if (start) run = t;
+        rep[2 * (D.snap0 + t) + side] = (int)run;
+    }
+}
+
+// Warp per (snapshot, side): copy the run's first row when this row is a copy.
+__global__ void k_copy_rows(DevScenes g, long long total_snap, const int *rep,
+                            unsigned long long *ctr)
+{
+    const long long item = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (item >= 2 * total_snap) return;
+    const long long T = item >> 1;
+    const int side = (int)(item & 1);
+    const SceneDesc &D = g.desc[scene_of_snap(g.desc, g.n_scenes, T)];
+    const long long t = T - D.snap0;
+    const long long r = rep[item];
+    if (r == t) return;
+    const uint32_t *srcrow = D.table + ((size_t)r * 2 + side) * D.W;
+    uint32_t *dst = D.table + ((size_t)t * 2 + side) * D.W;
+    for (int c = lane; c < D.W; c += 32) dst[c] = srcrow[c];
+    if (lane == 0) atomicAdd(ctr + C_DEDUP_ROWS, 1ull);
+}
+
+// ------------------------------------------------------------ launchers
+
+template <bool PERSIST, bool CACHE, class LeafFn>
+static void launch_one(const DevScenes &g, long long total_snap, long long items,
+                       const LaunchCfg &cfg, const int *rep, unsigned long long *work,
+                       unsigned long long *ctr, int *err, cudaStream_t st)
+{
     const int threads = 32 * cfg.warps_per_block;
-    if (cfg.persistent) {
+    auto kern = k_table<PERSIST, CACHE, LeafFn>;
+    if (PERSIST) {
         int per_sm = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_table<true, LeafFn>, threads, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, 0);
         int blocks = cfg.n_sm * (per_sm > 0 ? per_sm : 1);
         cudaMemsetAsync(work, 0, sizeof(unsigned long long), st);
-        k_table<true, LeafFn><<<blocks, threads, 0, st>>>(g, total_snap, items, cfg.tile, work,
-                                                         ctr, err);
+        kern<<<blocks, threads, 0, st>>>(g, total_snap, items, cfg.tile, rep, work, ctr, err);
     } else {
         long long blocks = (items + cfg.warps_per_block - 1) / cfg.warps_per_block;
-        k_table<false, LeafFn><<<(unsigned)blocks, threads, 0, st>>>(g, total_snap, items, 1, work,
-                                                                    ctr, err);
+        kern<<<(unsigned)blocks, threads, 0, st>>>(g, total_snap, items, 1, rep, work, ctr, err);
     }
-    note_launches(1);
-    return cudaGetLastError();
+}
+
+template <class LeafFn>
+static void launch_leaf(const DevScenes &g, long long total_snap, long long items,
+                        const LaunchCfg &cfg, const int *rep, unsigned long long *work,
+                        unsigned long long *ctr, int *err, cudaStream_t st)
+{
+    if (cfg.persistent) {
+        if (cfg.cache) launch_one<true, true, LeafFn>(g, total_snap, items, cfg, rep, work, ctr, err, st);
+        else launch_one<true, false, LeafFn>(g, total_snap, items, cfg, rep, work, ctr, err, st);
+    } else {
+        if (cfg.cache) launch_one<false, true, LeafFn>(g, total_snap, items, cfg, rep, work, ctr, err, st);
+        else launch_one<false, false, LeafFn>(g, total_snap, items, cfg, rep, work, ctr, err, st);
+    }
 }
 
 cudaError_t launch_table(const DevScenes &g, long long total_snap, long long total_los_chunks,
-                         const LaunchCfg &cfg, unsigned long long *work,
+                         const LaunchCfg &cfg, int *rep, unsigned long long *work,
                          unsigned long long *ctr, int *err, cudaStream_t st)
 {
+    const long long items = 2 * total_snap + total_los_chunks;
+    if (items == 0) return cudaSuccess;
+    int launched = 1;
+    if (cfg.dedup) {
+        k_runs<<<dim3(g.n_scenes, 2), 1024, 0, st>>>(g, rep);
+        launched++;
+    }
     if (cfg.mode == IVM_MODE_EXACT)
-        return launch_table_t<ExactLeaf>(g, total_snap, total_los_chunks, cfg, work, ctr, err, st);
-    return launch_table_t<FilteredLeaf>(g, total_snap, total_los_chunks, cfg, work, ctr, err, st);
+        launch_leaf<ExactLeaf>(g, total_snap, items, cfg, cfg.dedup ? rep : nullptr, work, ctr,
+                               err, st);
+    else
+        launch_leaf<FilteredLeaf>(g, total_snap, items, cfg, cfg.dedup ? rep : nullptr, work,
+                                  ctr, err, st);
+    if (cfg.dedup && total_snap > 0) {
+        long long warps = 2 * total_snap;
+        k_copy_rows<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, st>>>(g, total_snap, rep, ctr);
+        launched++;
+    }
+    note_launches(launched);
+    return cudaGetLastError();
 }
 
 }  // namespace ivm

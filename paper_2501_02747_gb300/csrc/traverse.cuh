@@ -27,8 +27,7 @@ struct Seg {
     int px, py, pz;
     int dx, dy, dz;
     float fpx, fpy, fpz;  // P as float: exact, |P| < 2^22
-    float ix, iy, iz;     // round-to-nearest reciprocal of d (0 where d == 0)
-    int zmask;            // bit a set where d_a == 0
+    float ix, iy, iz;     // round-to-nearest reciprocal of d; 2^100 where d == 0
 };
 
 __device__ __forceinline__ Seg make_seg(int px, int py, int pz, int qx, int qy, int qz)
@@ -37,39 +36,29 @@ __device__ __forceinline__ Seg make_seg(int px, int py, int pz, int qx, int qy, 
     s.px = px; s.py = py; s.pz = pz;
     s.dx = qx - px; s.dy = qy - py; s.dz = qz - pz;
     s.fpx = (float)px; s.fpy = (float)py; s.fpz = (float)pz;
-    s.zmask = (s.dx == 0) | ((s.dy == 0) << 1) | ((s.dz == 0) << 2);
-    s.ix = s.dx ? __frcp_rn((float)s.dx) : 0.f;
-    s.iy = s.dy ? __frcp_rn((float)s.dy) : 0.f;
-    s.iz = s.dz ? __frcp_rn((float)s.dz) : 0.f;
+    s.ix = s.dx ? __frcp_rn((float)s.dx) : 0x1p100f;
+    s.iy = s.dy ? __frcp_rn((float)s.dy) : 0x1p100f;
+    s.iz = s.dz ? __frcp_rn((float)s.dz) : 0x1p100f;
     return s;
 }
 
-// One axis of the slab test.  (l - p) is exact (integers below 2^24); the
-// product with the rounded reciprocal has relative error below 2^-23.
-__device__ __forceinline__ void slab_axis(float p, float inv, bool zero, float l, float h,
-                                          float &tn, float &tf)
-{
-    float t0 = __fmul_rn(l - p, inv), t1 = __fmul_rn(h - p, inv);
-    float n = fminf(t0, t1), f = fmaxf(t0, t1);
-    if (zero) {
-        bool in = (l <= p) & (p <= h);
-        n = in ? -kBig : kBig;
-        f = in ? kBig : -kBig;
-    }
-    tn = fmaxf(tn, n);
-    tf = fminf(tf, f);
-}
-
-// Conservative: true whenever the open segment touches the closed box.  The
-// entry/exit parameters carry relative error below 2^-23; widening them by
-// 2^-20 of their magnitude makes the test a superset of the exact one.
+// Conservative segment-box test: true whenever the open segment touches the
+// closed integer box.  Boxes are stored enlarged by half a unit (integer
+// bound -/+ 0.5; exact in float below 2^23), which gives the d = 0 axes
+// their answer without a branch: with 1/d replaced by 2^100, an axis where
+// the segment lies inside the slab gives (-huge, +huge) and one where it lies
+// outside gives an entry above 1 or an exit below 0.  For d != 0, (l - p) is
+// exact and the product with the rounded reciprocal has relative error below
+// 2^-23; widening entry and exit by 2^-20 of their magnitude makes the test a
+// superset of the exact one.
 __device__ __forceinline__ bool seg_box(const Seg &s, float lx, float ly, float lz, float hx,
                                         float hy, float hz)
 {
-    float tn = -kBig, tf = kBig;
-    slab_axis(s.fpx, s.ix, s.zmask & 1, lx, hx, tn, tf);
-    slab_axis(s.fpy, s.iy, s.zmask & 2, ly, hy, tn, tf);
-    slab_axis(s.fpz, s.iz, s.zmask & 4, lz, hz, tn, tf);
+    float ax = __fmul_rn(lx - s.fpx, s.ix), bx = __fmul_rn(hx - s.fpx, s.ix);
+    float ay = __fmul_rn(ly - s.fpy, s.iy), by = __fmul_rn(hy - s.fpy, s.iy);
+    float az = __fmul_rn(lz - s.fpz, s.iz), bz = __fmul_rn(hz - s.fpz, s.iz);
+    float tn = fmaxf(fmaxf(fminf(ax, bx), fminf(ay, by)), fminf(az, bz));
+    float tf = fminf(fminf(fmaxf(ax, bx), fmaxf(ay, by)), fmaxf(az, bz));
     float tnw = tn - fabsf(tn) * 0x1p-20f;
     float tfw = tf + fabsf(tf) * 0x1p-20f;
     return (tnw <= tfw) & (tnw < 1.f) & (tfw > 0.f);
@@ -172,7 +161,8 @@ __device__ __forceinline__ Leaf load_leaf(const Leaf *leaves, int g)
 
 // Per-lane test counts; summed over the warp once per task (flush_counters).
 struct WalkCounters {
-    unsigned long long node_tests = 0, leaf_tests = 0, undecided = 0, exact = 0, segments = 0;
+    unsigned long long node_tests = 0, leaf_tests = 0, undecided = 0, exact = 0, segments = 0,
+                       cache_hits = 0;
 };
 
 __device__ __forceinline__ unsigned long long warp_sum(unsigned long long v)
@@ -185,8 +175,9 @@ __device__ __forceinline__ void flush_counters(WalkCounters &wc, unsigned long l
 {
     unsigned long long a = warp_sum(wc.node_tests), b = warp_sum(wc.leaf_tests),
                        c = warp_sum(wc.undecided), d = warp_sum(wc.exact),
-                       e = warp_sum(wc.segments);
+                       e = warp_sum(wc.segments), f = warp_sum(wc.cache_hits);
     if ((threadIdx.x & 31) == 0) {
+        if (f) atomicAdd(ctr + C_CACHE_HITS, f);
         if (a) atomicAdd(ctr + C_NODE_TESTS, a);
         if (b) atomicAdd(ctr + C_LEAF_TESTS, b);
         if (c) atomicAdd(ctr + C_UNDECIDED, c);
@@ -206,11 +197,12 @@ template <class LeafFn>
 __device__ __forceinline__ unsigned walk_packet(const Seg &s, unsigned alive, const Node *nodes,
                                                 const Leaf *leaves, int root, float dirx,
                                                 float diry, float dirz, int budget, int *err,
-                                                WalkCounters &wc, LeafFn leaf_hit)
+                                                WalkCounters &wc, LeafFn leaf_hit, int &blocker)
 {
     const int lane = threadIdx.x & 31;
     int s0 = 0, s1 = 0, sp = 0;   // stack: entry k lives in lane k&31 of s0 / s1
     int node = root;
+    blocker = -1;
     while (alive) {
         if (--budget < 0) {
             if (lane == 0) raise_error(err, IVM_ERR_TIMEOUT);
@@ -222,7 +214,9 @@ __device__ __forceinline__ unsigned walk_packet(const Seg &s, unsigned alive, co
             bool me = (alive >> lane) & 1u;
             bool hit = me && leaf_hit(s, L, wc);
             wc.leaf_tests += me;
-            alive &= ~__ballot_sync(kFull, hit);
+            const unsigned hm = __ballot_sync(kFull, hit);
+            if (hm) blocker = ~node;
+            alive &= ~hm;
         } else {
             const float4 *np = reinterpret_cast<const float4 *>(nodes + node);
             float4 A = __ldg(np), B = __ldg(np + 1), C = __ldg(np + 2);
@@ -262,6 +256,75 @@ __device__ __forceinline__ unsigned walk_packet(const Seg &s, unsigned alive, co
             node = sp < 32 ? v0 : v1;
         }
     }
+    return alive;
+}
+
+// Occluder cache: the facets that most recently blocked a segment of this
+// warp (warp-uniform, most recent first).  Neighbouring packets -- the next
+// sample pairs of the same facet pair, the next facet of the same row -- are
+// often blocked by the same building, so testing these few facets first
+// settles most blocked lanes without a BVH walk.  A cached facet is tested
+// with the same exact leaf test, so the result never depends on the cache.
+constexpr int kCacheSize = 4;
+
+struct OccluderCache {
+    int f[kCacheSize];
+    int scene = -1;   // facets are global indices: the cache belongs to one scene
+    __device__ __forceinline__ OccluderCache()
+    {
+        for (int k = 0; k < kCacheSize; k++) f[k] = -1;
+    }
+    // Call at the start of every work item (warp-uniform).
+    __device__ __forceinline__ void enter_scene(int sc)
+    {
+        if (sc == scene) return;
+        scene = sc;
+        for (int k = 0; k < kCacheSize; k++) f[k] = -1;
+    }
+    __device__ __forceinline__ void put(int g)
+    {
+        if (g < 0 || g == f[0]) return;
+        int prev = g;
+        for (int k = 0; k < kCacheSize; k++) {   // move-to-front, dropping the oldest
+            int cur = f[k];
+            f[k] = prev;
+            if (cur == g) break;
+            prev = cur;
+        }
+    }
+};
+
+// Lanes of the packet left unblocked: cached occluders first (when `cache`),
+// then the BVH walk.  Same contract as walk_packet.
+template <bool CACHE, class LeafFn>
+__device__ __forceinline__ unsigned occlude(const Seg &s, unsigned alive, const Node *nodes,
+                                            const Leaf *leaves, int root, float dirx, float diry,
+                                            float dirz, int budget, int *err, WalkCounters &wc,
+                                            LeafFn leaf_hit, OccluderCache &cache)
+{
+    const int lane = threadIdx.x & 31;
+    if (CACHE) {
+        int promote = -1;
+#pragma unroll
+        for (int k = 0; k < kCacheSize; k++) {
+            const int g = cache.f[k];
+            if (!alive || g < 0) break;
+            const Leaf L = load_leaf(leaves, g);
+            bool me = (alive >> lane) & 1u;
+            bool hit = me && leaf_hit(s, L, wc);
+            wc.leaf_tests += me;
+            wc.cache_hits += hit;
+            const unsigned hm = __ballot_sync(kFull, hit);
+            alive &= ~hm;
+            if (hm && k > 0 && promote < 0) promote = g;
+        }
+        if (promote >= 0) cache.put(promote);   // the facet that worked moves to the front
+        if (!alive) return 0;
+    }
+    int blocker;
+    alive = walk_packet(s, alive, nodes, leaves, root, dirx, diry, dirz, budget, err, wc,
+                        leaf_hit, blocker);
+    if (CACHE) cache.put(blocker);
     return alive;
 }
 

@@ -18,7 +18,7 @@ from . import build as _build
 IVM_OK, IVM_ERR_ARG, IVM_ERR_RANGE, IVM_ERR_CAPACITY = 0, 1, 2, 3
 IVM_ERR_TIMEOUT, IVM_ERR_CUDA, IVM_ERR_INTERNAL = 4, 5, 6
 IVM_MODE_EXACT, IVM_MODE_FILTERED, IVM_MODE_LEARNED = 0, 1, 2
-IVM_FLAG_PERSISTENT, IVM_FLAG_GRAPH = 1, 2
+IVM_FLAG_PERSISTENT, IVM_FLAG_GRAPH, IVM_FLAG_OCCLUDER_CACHE, IVM_FLAG_DEDUP_SOURCES = 1, 2, 4, 8
 
 
 class ivm_facet(ctypes.Structure):
@@ -41,6 +41,7 @@ class ivm_stats(ctypes.Structure):
                 ("segments", ctypes.c_uint64), ("node_tests", ctypes.c_uint64),
                 ("leaf_tests", ctypes.c_uint64), ("undecided", ctypes.c_uint64),
                 ("exact_tests", ctypes.c_uint64), ("ranker_hits", ctypes.c_uint64),
+                ("cache_hits", ctypes.c_uint64), ("dedup_rows", ctypes.c_uint64),
                 ("ms_ingest", ctypes.c_float), ("ms_bvh", ctypes.c_float),
                 ("ms_screen", ctypes.c_float), ("ms_traverse", ctypes.c_float),
                 ("ms_tree", ctypes.c_float), ("ms_total", ctypes.c_float)]

@@ -16,6 +16,9 @@ from tests.gpu_common import padding_is_zero, to_np, unpack
 pytestmark = pytest.mark.gpu
 
 MODES = [ivm.IVM_MODE_EXACT, ivm.IVM_MODE_FILTERED]
+FAST = ivm.IVM_FLAG_PERSISTENT | ivm.IVM_FLAG_OCCLUDER_CACHE | ivm.IVM_FLAG_DEDUP_SOURCES
+FLAG_SETS = [0, ivm.IVM_FLAG_PERSISTENT, ivm.IVM_FLAG_OCCLUDER_CACHE,
+             ivm.IVM_FLAG_DEDUP_SOURCES, FAST]
 
 
 @pytest.fixture(scope="module")
@@ -60,15 +63,17 @@ def test_tx_inside_footprint(ctx):
 
 
 @pytest.mark.parametrize("mode", MODES)
-@pytest.mark.parametrize("persistent", [0, ivm.IVM_FLAG_PERSISTENT])
-def test_tiny_workload_full(ctx, mode, persistent):
+@pytest.mark.parametrize("flags", FLAG_SETS)
+def test_tiny_workload_full(ctx, mode, flags):
     sc = sg.tiny()
-    M, st = gpu_matrix(ctx, sc.facets, 3, mode, persistent)
+    M, st = gpu_matrix(ctx, sc.facets, 3, mode, flags)
     assert (M == oracle.matrix(sc.facets, 3)).all()
     assert st.pairs == sc.n_facets ** 2 and st.cand_pairs > 0
-    T, L, _ = gpu_table(ctx, sc.facets, 3, sc.tx, sc.rx, mode, persistent)
+    T, L, stt = gpu_table(ctx, sc.facets, 3, sc.tx, sc.rx, mode, flags)
     tab, los = oracle.table(sc.facets, 3, sc.tx, sc.rx)
     assert (T == tab).all() and (L == los).all()
+    if flags & ivm.IVM_FLAG_DEDUP_SOURCES:
+        assert stt.dedup_rows == sc.n_snap - 1      # the Tx is static: one row traced
 
 
 @pytest.mark.parametrize("seed,nb,s", [(401, 3, 1), (402, 6, 2), (403, 7, 3), (404, 13, 2),
@@ -79,11 +84,26 @@ def test_random_small_scenes_full(ctx, seed, nb, s):
     want = oracle.matrix(sc.facets, s)
     tab, los = oracle.table(sc.facets, s, sc.tx, sc.rx)
     for mode in MODES:
-        M, _ = gpu_matrix(ctx, sc.facets, s, mode)
-        assert (M == want).all(), mode
-        assert padding_is_zero(M, sc.n_facets)
-        T, L, _ = gpu_table(ctx, sc.facets, s, sc.tx, sc.rx, mode)
-        assert (T == tab).all() and (L == los).all(), mode
+        for flags in (0, FAST):
+            M, _ = gpu_matrix(ctx, sc.facets, s, mode, flags)
+            assert (M == want).all(), (mode, flags)
+            assert padding_is_zero(M, sc.n_facets)
+            T, L, _ = gpu_table(ctx, sc.facets, s, sc.tx, sc.rx, mode, flags)
+            assert (T == tab).all() and (L == los).all(), (mode, flags)
+
+
+def test_dedup_with_runs_of_equal_positions(ctx):
+    """Paused movers: runs of equal positions of uneven length on both sides."""
+    sc = sg.random_small_city(431, n_buildings=5, side=9000, n_snap=12, s=2)
+    idx_tx = np.repeat(np.arange(12), [1, 3, 1, 1, 7, 2, 1, 1, 4, 1, 1, 2])[:20]
+    idx_rx = np.repeat(np.arange(12), [2, 1, 5, 1, 1, 1, 3, 1, 1, 2, 1, 1])[:20]
+    tx, rx = sc.tx[idx_tx], sc.rx[idx_rx]
+    tab, los = oracle.table(sc.facets, 2, tx, rx)
+    for flags in (ivm.IVM_FLAG_DEDUP_SOURCES, FAST):
+        T, L, st = gpu_table(ctx, sc.facets, 2, tx, rx, ivm.IVM_MODE_FILTERED, flags)
+        assert (T == tab).all() and (L == los).all()
+        runs = sum(1 + int((np.diff(a, axis=0) != 0).any(axis=1).sum()) for a in (tx, rx))
+        assert st.dedup_rows == 2 * 20 - runs
 
 
 def test_many_samples_table_path(ctx):
@@ -146,7 +166,7 @@ def test_range_errors(ctx):
 def test_batched_scenes_equal_single_calls(ctx, mode):
     scenes = [sg.random_small_city(420 + k, n_buildings=2 + 3 * k, side=8000, n_snap=5 + 7 * k, s=2)
               for k in range(4)]
-    for flags in (0, ivm.IVM_FLAG_PERSISTENT):
+    for flags in (0, ivm.IVM_FLAG_PERSISTENT, FAST):
         Ms, _ = ivm.ivm_build_matrix(ctx, [sc.facets for sc in scenes], 2, mode=mode, flags=flags)
         outs, _ = ivm.ivm_build_table(ctx, [sc.facets for sc in scenes], 2,
                                       [sc.tx for sc in scenes], [sc.rx for sc in scenes],
@@ -185,10 +205,9 @@ def _sample_pairs(rng, M, n, k):
 def district_gpu(ctx):
     sc = sg.district()
     M, st = gpu_matrix(ctx, sc.facets, 5)
-    Mf, stf = gpu_matrix(ctx, sc.facets, 5, ivm.IVM_MODE_FILTERED, ivm.IVM_FLAG_PERSISTENT)
+    Mf, stf = gpu_matrix(ctx, sc.facets, 5, ivm.IVM_MODE_FILTERED, FAST)
     T, L, _ = gpu_table(ctx, sc.facets, 5, sc.tx, sc.rx)
-    Tf, Lf, _ = gpu_table(ctx, sc.facets, 5, sc.tx, sc.rx, ivm.IVM_MODE_FILTERED,
-                          ivm.IVM_FLAG_PERSISTENT)
+    Tf, Lf, _ = gpu_table(ctx, sc.facets, 5, sc.tx, sc.rx, ivm.IVM_MODE_FILTERED, FAST)
     return sc, M, Mf, T, L, Tf, Lf, st
 
 
@@ -229,6 +248,8 @@ def test_degenerate_filtered_equals_exact_and_oracle(ctx):
     M, st = gpu_matrix(ctx, sc.facets, 5)
     Mf, stf = gpu_matrix(ctx, sc.facets, 5, ivm.IVM_MODE_FILTERED)
     assert (M == Mf).all()
+    Mc, _ = gpu_matrix(ctx, sc.facets, 5, ivm.IVM_MODE_FILTERED, FAST)
+    assert (M == Mc).all()
     assert stf.undecided > 0          # the seeded near-degenerate cases reach the fallback
     # rows of the degenerately placed buildings (ids 190..199) against the oracle
     deg_rows = np.flatnonzero(sc.facets[:, 9] >= 190)

@@ -51,6 +51,10 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    # profiling case: one phase of one form on the first N snapshots (no JSON contract line)
+    p.add_argument("--profile", choices=["matrix", "table", "tree"], default=None)
+    p.add_argument("--form", choices=["fast", "plain"], default="fast")
+    p.add_argument("--snapshots", type=int, default=None)
     return p.parse_args()
 
 
@@ -238,6 +242,28 @@ def run_ours(args, ws, rank, local):
         _, stt = ivm.ivm_build_table(ctx, fac, s, tx, rx, out=(T, L), **kw)
         ivm.ivm_expand_image_tree(ctx, M, T, L, N, K, summary=summ)
         return stm, stt
+
+    if args.profile:
+        # small profiling case: one phase, first --snapshots snapshots
+        Sp = min(S, args.snapshots or S)
+        kw = forms[args.form]
+        for _ in range(args.warmup + args.steps):
+            if args.profile == "matrix":
+                _, st = ivm.ivm_build_matrix(ctx, facets_d, s, out=M_d, **kw)
+            elif args.profile == "table":
+                _, st = ivm.ivm_build_table(ctx, facets_d, s, tx_d[:Sp], rx_d[:Sp],
+                                            out=(T_d[:Sp], L_d[:Sp]), **kw)
+            else:
+                ivm.ivm_build_matrix(ctx, facets_d, s, out=M_d, **kw)
+                ivm.ivm_build_table(ctx, facets_d, s, tx_d[:Sp], rx_d[:Sp],
+                                    out=(T_d[:Sp], L_d[:Sp]), **kw)
+                ivm.ivm_expand_image_tree(ctx, M_d, T_d[:Sp], L_d[:Sp], N, K, summary=summ_d[:Sp])
+                st = None
+        torch.cuda.synchronize()
+        print(json.dumps({"profile": args.profile, "form": args.form, "snapshots": Sp,
+                          "stats": st.as_dict() if st is not None else None}))
+        ctx.close()
+        return
 
     def timed(form):
         for _ in range(args.warmup):

@@ -65,7 +65,16 @@ __global__ void k_morton(DevScenes g, const int *bounds)
         q[a] = span > 0 ? (unsigned)(((c - lo) * 1023) / span) : 0u;
     }
     unsigned long long code = spread10(q[0]) | (spread10(q[1]) << 1) | (spread10(q[2]) << 2);
-    g.keys[f] = (code << 32) | (unsigned)(f - g.desc[sc].facet0);
+    // A facet spanning more than 1/4 of the scene in x or y (the ground) would
+    // give every ancestor in the Morton order a scene-sized box; its key gets
+    // the top bit so the root splits such facets off into their own subtree.
+    bool large = false;
+    for (int a = 0; a < 2; a++) {
+        long long ext = 2LL * ((long long)b[3 + a] - b[a]);   // in centroid (lo + hi) units
+        long long span = (long long)B[3 + a] - B[a];
+        large |= span > 0 && 4 * ext > span;
+    }
+    g.keys[f] = (large ? (1ull << 63) : 0ull) | (code << 32) | (unsigned)(f - g.desc[sc].facet0);
 }
 
 // grid (ceil(maxN / 256), n_scenes): thread = one key of scene blockIdx.y

@@ -40,6 +40,29 @@ __device__ __forceinline__ int orient_filtered(float ax, float ay, float az, flo
     return e > bound ? 1 : (e < -bound ? -1 : 0);
 }
 
+// The rare path: some edge orientation was undecided and the decided ones
+// agree; recompute the undecided ones exactly.  Out of line so that its
+// int128 registers do not count against the traversal loop.
+// Arguments by value (corner O - P, edges U and V, direction d, the four
+// float verdicts packed as 2-bit fields) so nothing is spilled to the stack.
+static __device__ __noinline__ bool settle_exact(int c0x, int c0y, int c0z, int ux, int uy,
+                                                 int uz, int vx, int vy, int vz, int dx, int dy,
+                                                 int dz, int packed)
+{
+    int e0 = ((packed >> 0) & 3) - 1, e1 = ((packed >> 2) & 3) - 1;
+    int e2 = ((packed >> 4) & 3) - 1, e3 = ((packed >> 6) & 3) - 1;
+    int c1x = c0x + ux, c1y = c0y + uy, c1z = c0z + uz;
+    int c2x = c1x + vx, c2y = c1y + vy, c2z = c1z + vz;
+    int c3x = c0x + vx, c3y = c0y + vy, c3z = c0z + vz;
+    if (e0 == 0) e0 = orient_sign(c0x, c0y, c0z, c1x, c1y, c1z, dx, dy, dz);
+    if (e1 == 0) e1 = orient_sign(c1x, c1y, c1z, c2x, c2y, c2z, dx, dy, dz);
+    if (e2 == 0) e2 = orient_sign(c2x, c2y, c2z, c3x, c3y, c3z, dx, dy, dz);
+    if (e3 == 0) e3 = orient_sign(c3x, c3y, c3z, c0x, c0y, c0z, dx, dy, dz);
+    bool nonneg = (e0 >= 0) & (e1 >= 0) & (e2 >= 0) & (e3 >= 0);
+    bool nonpos = (e0 <= 0) & (e1 <= 0) & (e2 <= 0) & (e3 <= 0);
+    return nonneg | nonpos;
+}
+
 __device__ __forceinline__ bool facet_hit_filtered(const Seg &s, const Leaf &L, WalkCounters &wc)
 {
     long long rx = s.px - L.ox, ry = s.py - L.oy, rz = s.pz - L.oz;
@@ -52,14 +75,11 @@ __device__ __forceinline__ bool facet_hit_filtered(const Seg &s, const Leaf &L, 
         return coplanar_hit(s, L);
     }
     if (a == 0 || b == 0) return false;
-    int c0x = L.ox - s.px, c0y = L.oy - s.py, c0z = L.oz - s.pz;
-    int c1x = c0x + L.ux, c1y = c0y + L.uy, c1z = c0z + L.uz;
-    int c2x = c1x + L.vx, c2y = c1y + L.vy, c2z = c1z + L.vz;
-    int c3x = c0x + L.vx, c3y = c0y + L.vy, c3z = c0z + L.vz;
-    float f0x = (float)c0x, f0y = (float)c0y, f0z = (float)c0z;
-    float f1x = (float)c1x, f1y = (float)c1y, f1z = (float)c1z;
-    float f2x = (float)c2x, f2y = (float)c2y, f2z = (float)c2z;
-    float f3x = (float)c3x, f3y = (float)c3y, f3z = (float)c3z;
+    // corners relative to P: integers below 2^23, exact in float
+    float f0x = (float)(L.ox - s.px), f0y = (float)(L.oy - s.py), f0z = (float)(L.oz - s.pz);
+    float f1x = f0x + (float)L.ux, f1y = f0y + (float)L.uy, f1z = f0z + (float)L.uz;
+    float f2x = f1x + (float)L.vx, f2y = f1y + (float)L.vy, f2z = f1z + (float)L.vz;
+    float f3x = f0x + (float)L.vx, f3y = f0y + (float)L.vy, f3z = f0z + (float)L.vz;
     float dx = (float)s.dx, dy = (float)s.dy, dz = (float)s.dz;
     int e0 = orient_filtered(f0x, f0y, f0z, f1x, f1y, f1z, dx, dy, dz);
     int e1 = orient_filtered(f1x, f1y, f1z, f2x, f2y, f2z, dx, dy, dz);
@@ -72,13 +92,9 @@ __device__ __forceinline__ bool facet_hit_filtered(const Seg &s, const Leaf &L, 
     // some edge is undecided and the decided ones agree: settle it exactly
     wc.undecided++;
     wc.exact++;
-    if (e0 == 0) e0 = orient_sign(c0x, c0y, c0z, c1x, c1y, c1z, s.dx, s.dy, s.dz);
-    if (e1 == 0) e1 = orient_sign(c1x, c1y, c1z, c2x, c2y, c2z, s.dx, s.dy, s.dz);
-    if (e2 == 0) e2 = orient_sign(c2x, c2y, c2z, c3x, c3y, c3z, s.dx, s.dy, s.dz);
-    if (e3 == 0) e3 = orient_sign(c3x, c3y, c3z, c0x, c0y, c0z, s.dx, s.dy, s.dz);
-    bool nonneg = (e0 >= 0) & (e1 >= 0) & (e2 >= 0) & (e3 >= 0);
-    bool nonpos = (e0 <= 0) & (e1 <= 0) & (e2 <= 0) & (e3 <= 0);
-    return nonneg | nonpos;
+    const int packed = (e0 + 1) | ((e1 + 1) << 2) | ((e2 + 1) << 4) | ((e3 + 1) << 6);
+    return settle_exact(L.ox - s.px, L.oy - s.py, L.oz - s.pz, L.ux, L.uy, L.uz, L.vx, L.vy, L.vz,
+                        s.dx, s.dy, s.dz, packed);
 }
 
 struct FilteredLeaf {

@@ -389,7 +389,8 @@ extern "C" int ivm_build_table(ivm_ctx *c, const ivm_scene *scenes, int32_t n_sc
     DevScenes g;
     std::vector<SceneDesc> hd;
     if ((r = setup_geometry(c, scenes, n_scenes, params->samples_per_side, g, hd))) return r;
-    long long snaps = 0, chunks = 0;
+    long long snaps = 0, chunks = 0, items = 0;
+    const int snap_tile = params->tile > 0 ? params->tile : 16;
     size_t host_tab = 0, host_los = 0, pos_tx = 0, pos_rx = 0;
     std::vector<char> tab_host(n_scenes), los_host(n_scenes), tx_host(n_scenes),
         rx_host(n_scenes);
@@ -399,8 +400,11 @@ extern "C" int ivm_build_table(ivm_ctx *c, const ivm_scene *scenes, int32_t n_sc
         hd[k].snap0 = snaps;
         hd[k].nsnap = n_snap[k];
         hd[k].los0 = chunks;
+        hd[k].item0 = items;
+        hd[k].ntiles = (int)((n_snap[k] + snap_tile - 1) / snap_tile);
         snaps += n_snap[k];
         chunks += (n_snap[k] + 31) / 32;
+        items += 2LL * hd[k].W * hd[k].ntiles;
         const size_t S = (size_t)n_snap[k];
         if (S == 0) continue;
         tab_host[k] = !is_device(table[k]);
@@ -448,8 +452,8 @@ extern "C" int ivm_build_table(ivm_ctx *c, const ivm_scene *scenes, int32_t n_sc
     if ((r = build_geometry(c, g))) return r;
     const LaunchCfg cfg = launch_cfg(c, params);
     if (cfg.dedup && (r = ensure(c, S_REP, sizeof(int) * 2 * (size_t)snaps))) return r;
-    CK(launch_table(g, snaps, chunks, cfg, ptr<int>(c, S_REP), c->d_misc + 2, c->d_ctr, c->d_err,
-                    c->stream));
+    CK(launch_table(g, snaps, items, chunks, snap_tile, cfg, ptr<int>(c, S_REP), c->d_misc + 2,
+                    c->d_ctr, c->d_err, c->stream));
     CK(cudaEventRecord(c->ev[4], c->stream));
     if ((r = read_error(c))) return r;
     for (int k = 0; k < n_scenes; k++) {

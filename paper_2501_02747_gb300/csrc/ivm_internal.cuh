@@ -48,7 +48,8 @@ struct SceneDesc {
     int root;         // node reference of the root
     int s;            // samples per side
     int sample0;      // first global sample index (n * s * s samples)
-    int pad;
+    int ntiles;       // table: tiles of consecutive snapshots, ceil(nsnap / tile)
+    long long item0;  // table: first work item; the scene has 2 * W * ntiles items
     long long rw0;    // first (row, word) index of this scene: n * W of them
     long long los0;   // first 32-snapshot LoS chunk of this scene
     uint32_t *matrix; // output rows [n][W]
@@ -123,8 +124,9 @@ struct LaunchCfg {
 cudaError_t launch_matrix(const DevScenes &g, const int2 *pairs, unsigned long long npairs,
                           const LaunchCfg &cfg, unsigned long long *work,
                           unsigned long long *ctr, int *err, cudaStream_t st);
-cudaError_t launch_table(const DevScenes &g, long long total_snap, long long total_los_chunks,
-                         const LaunchCfg &cfg, int *rep, unsigned long long *work,
-                         unsigned long long *ctr, int *err, cudaStream_t st);
+cudaError_t launch_table(const DevScenes &g, long long total_snap, long long total_items,
+                         long long total_los_chunks, int snap_tile, const LaunchCfg &cfg,
+                         int *rep, unsigned long long *work, unsigned long long *ctr, int *err,
+                         cudaStream_t st);
 
 }  // namespace ivm

@@ -46,8 +46,9 @@ __device__ __forceinline__ void decide_pair(const DevScenes &g, int gi, int gj, 
         if (!alive) continue;
         wc.segments += face;
         const Seg sg = make_seg(px, py, pz, qx, qy, qz);
+        int myblk = -1;
         alive = occlude<CACHE>(sg, alive, g.nodes, g.leaf, D.root, dirx, diry, dirz, budget, err,
-                               wc, leaf, cache);
+                               wc, leaf, cache, myblk);
         if (alive) {
             visible = true;
             break;
@@ -60,7 +61,8 @@ __device__ __forceinline__ void decide_pair(const DevScenes &g, int gi, int gj, 
 }
 
 template <bool PERSIST, bool CACHE, class LeafFn>
-__global__ void k_matrix(DevScenes g, const int2 *pairs, unsigned long long npairs, int tile,
+__global__ void __launch_bounds__(kTravThreads, IVM_MIN_BLOCKS)
+k_matrix(DevScenes g, const int2 *pairs, unsigned long long npairs, int tile,
                          unsigned long long *work, unsigned long long *ctr, int *err)
 {
     WalkCounters wc;

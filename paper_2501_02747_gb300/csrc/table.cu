@@ -6,11 +6,19 @@
 // Tx_t - Rx_t segment is free (Sec. III-B: the transmitter is the parent node
 // that searches its reference faces).
 //
-// One warp per (snapshot, side).  It screens 32 facets per step with one
-// facing test per lane, then takes the front-facing facets a packet at a
-// time: with s*s <= 32 samples, floor(32 / (s*s)) facets share a packet; with
-// more samples a facet takes several packets and stops at the first free one.
-// Each 32-facet word of the row is written once, by lane 0.
+// Work item = (side, 32-facet word c, tile of consecutive snapshots).  Lane l
+// owns facet 32c + l: it does the facing test, and the warp then takes the
+// front-facing facets a packet at a time -- with s*s <= 32 samples,
+// floor(32 / (s*s)) facets share a packet; with more samples a facet takes
+// several packets and stops at the first free one.  Lane 0 writes the word.
+//
+// Along a trajectory the table changes only at ray creation and suppression
+// points (Sec. III-C); between them consecutive snapshots see the same
+// facets through the same gaps.  With the occluder cache on, lane l also
+// keeps the facet that blocked facet 32c + l at the previous snapshot of the
+// tile and tests it first: a blocked facet usually stays blocked by the same
+// building, so one exact facet test replaces the BVH walk.  The cached facet
+// is only tested, never trusted: a lane it does not block goes on to the walk.
 //
 // Runs of equal positions (a static Tx, a receiver that pauses) have equal
 // rows: with deduplication on, a pre-pass finds the first snapshot of each
@@ -31,6 +39,16 @@ __device__ __forceinline__ int scene_of_snap(const SceneDesc *desc, int n_scenes
     return lo;
 }
 
+__device__ __forceinline__ int scene_of_item(const SceneDesc *desc, int n_scenes, long long it)
+{
+    int lo = 0, hi = n_scenes - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (desc[mid].item0 <= it) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
 __device__ __forceinline__ int scene_of_los(const SceneDesc *desc, int n_scenes, long long c)
 {
     int lo = 0, hi = n_scenes - 1;
@@ -47,35 +65,79 @@ __device__ __forceinline__ bool in_range(long long x, long long y, long long z)
            (z > -kCoordLimit) & (z < kCoordLimit);
 }
 
+// Packet of segments from (x, y, z) to samples of facets of word c; returns
+// the lanes left unblocked.  Tests the lane's temporal blocker `tb` first.
 template <bool CACHE, class LeafFn>
-__device__ __forceinline__ void table_item(const DevScenes &g, long long item, const int *rep,
-                                           int *err, WalkCounters &wc, LeafFn leaf,
-                                           OccluderCache &cache)
+__device__ __forceinline__ unsigned table_packet(const DevScenes &g, const SceneDesc &D, bool mine,
+                                                 int sidx, int lead, int x, int y, int z,
+                                                 int tb, int *err, WalkCounters &wc,
+                                                 LeafFn leaf, OccluderCache &cache, int &myblk)
+{
+    int qx = 0, qy = 0, qz = 0;
+    if (mine) { qx = __ldg(g.sx + sidx); qy = __ldg(g.sy + sidx); qz = __ldg(g.sz + sidx); }
+    unsigned alive = __ballot_sync(kFull, mine);
+    wc.segments += mine;
+    const Seg sg = make_seg(x, y, z, qx, qy, qz);
+    myblk = -1;
+    if (CACHE) {
+        bool hit = false;
+        if (mine && tb >= 0) {
+            wc.leaf_tests++;
+            hit = leaf(sg, load_leaf(g.leaf, tb), wc);
+        }
+        if (hit) { myblk = tb; wc.cache_hits++; }
+        alive &= ~__ballot_sync(kFull, hit);
+        if (!alive) return 0;
+    }
+    const Leaf Lf = load_leaf(g.leaf, lead);
+    const float dirx = (float)(2 * Lf.ox + Lf.ux + Lf.vx - 2 * x);
+    const float diry = (float)(2 * Lf.oy + Lf.uy + Lf.vy - 2 * y);
+    const float dirz = (float)(2 * Lf.oz + Lf.uz + Lf.vz - 2 * z);
+    return occlude<CACHE>(sg, alive, g.nodes, g.leaf, D.root, dirx, diry, dirz, 4 * D.n + 16, err,
+                          wc, leaf, cache, myblk);
+}
+
+template <bool CACHE, class LeafFn>
+__device__ __forceinline__ void table_tile(const DevScenes &g, long long item, int TT,
+                                           const int *rep, int *err, WalkCounters &wc,
+                                           LeafFn leaf, OccluderCache &cache)
 {
     const int lane = threadIdx.x & 31;
-    const long long T = item >> 1;
-    const int side = (int)(item & 1);
-    const int sc = scene_of_snap(g.desc, g.n_scenes, T);
+    const int sc = scene_of_item(g.desc, g.n_scenes, item);
     const SceneDesc &D = g.desc[sc];
-    const long long t = T - D.snap0;
-    if (rep && rep[item] != t) return;          // a copy of its run's first row
+    const long long local = item - D.item0;
+    const long long per_side = (long long)D.W * D.ntiles;
+    const int side = local >= per_side ? 1 : 0;
+    const long long rem = local - side * per_side;
+    const int c = (int)(rem / D.ntiles);
+    const long long t0 = (rem - (long long)c * D.ntiles) * TT;
+    const long long t1 = min(t0 + TT, D.nsnap);
     if (CACHE) cache.enter_scene(sc);
-    const int *src = (side ? D.rx : D.tx) + 3 * t;
-    const long long k = 2LL * D.s;
-    const long long X0 = k * src[0], X1 = k * src[1], X2 = k * src[2];
-    uint32_t *row = D.table + ((size_t)t * 2 + side) * D.W;
-    if (!in_range(X0, X1, X2)) {
-        if (lane == 0) raise_error(err, IVM_ERR_RANGE);
-        for (int c = lane; c < D.W; c += 32) row[c] = 0u;
-        return;
+    const int *pos = side ? D.rx : D.tx;
+    const int jl = 32 * c + lane;
+    const bool has = jl < D.n;
+    int fnx = 0, fny = 0, fnz = 0, fox = 0, foy = 0, foz = 0;
+    if (has) {
+        const Leaf L = load_leaf(g.leaf, D.facet0 + jl);
+        fnx = L.nx; fny = L.ny; fnz = L.nz; fox = L.ox; foy = L.oy; foz = L.oz;
     }
-    const int x = (int)X0, y = (int)X1, z = (int)X2;
     const int s2 = D.s * D.s;
-    const int budget = 4 * D.n + 16;
-    for (int c = 0; c < D.W; c++) {
-        const int jl = 32 * c + lane;
-        bool fr = false;
-        if (jl < D.n) fr = front_of(load_leaf(g.leaf, D.facet0 + jl), x, y, z);
+    const long long k = 2LL * D.s;
+    int prev_blk = -1;   // lane l: facet that last blocked facet 32c + l
+    for (long long t = t0; t < t1; t++) {
+        if (rep && rep[2 * (D.snap0 + t) + side] != t) continue;   // copied later
+        uint32_t *row = D.table + ((size_t)t * 2 + side) * D.W;
+        const long long X0 = k * pos[3 * t], X1 = k * pos[3 * t + 1], X2 = k * pos[3 * t + 2];
+        if (!in_range(X0, X1, X2)) {
+            if (lane == 0) {
+                raise_error(err, IVM_ERR_RANGE);
+                row[c] = 0u;
+            }
+            continue;
+        }
+        const int x = (int)X0, y = (int)X1, z = (int)X2;
+        const bool fr = has && ((long long)fnx * (x - fox) + (long long)fny * (y - foy) +
+                                (long long)fnz * (z - foz)) > 0;
         unsigned fm = __ballot_sync(kFull, fr);
         unsigned word = 0;
         while (fm) {
@@ -88,47 +150,44 @@ __device__ __forceinline__ void table_item(const DevScenes &g, long long item, c
                 for (int q = 0; q < gi && q < 31; q++) m &= m - 1;
                 const int jbit = mine ? __ffs(m) - 1 : 0;
                 const int sidx = D.sample0 + (32 * c + jbit) * s2 + b;
-                int qx = 0, qy = 0, qz = 0;
-                if (mine) { qx = __ldg(g.sx + sidx); qy = __ldg(g.sy + sidx); qz = __ldg(g.sz + sidx); }
-                unsigned alive = __ballot_sync(kFull, mine);
+                const int tb = __shfl_sync(kFull, prev_blk, jbit);
                 const int lead = D.facet0 + 32 * c + __shfl_sync(kFull, jbit, 0);
-                const Leaf Lf = load_leaf(g.leaf, lead);
-                const float dirx = (float)(2 * Lf.ox + Lf.ux + Lf.vx - 2 * x);
-                const float diry = (float)(2 * Lf.oy + Lf.uy + Lf.vy - 2 * y);
-                const float dirz = (float)(2 * Lf.oz + Lf.uz + Lf.vz - 2 * z);
-                wc.segments += mine;
-                const Seg sg = make_seg(x, y, z, qx, qy, qz);
-                alive = occlude<CACHE>(sg, alive, g.nodes, g.leaf, D.root, dirx, diry, dirz,
-                                       budget, err, wc, leaf, cache);
+                int myblk;
+                const unsigned alive = table_packet<CACHE>(g, D, mine, sidx, lead, x, y, z, tb,
+                                                           err, wc, leaf, cache, myblk);
                 const unsigned smask = (s2 == 32) ? kFull : ((1u << s2) - 1u);
                 const bool gvis = mine && ((alive >> (gi * s2)) & smask) != 0u;
-                const unsigned bitv = (gvis && b == 0) ? (1u << jbit) : 0u;
-                word |= __reduce_or_sync(kFull, bitv);
+                word |= __reduce_or_sync(kFull, (gvis && b == 0) ? (1u << jbit) : 0u);
+                if (CACHE) {
+                    for (int q = 0; q < cnt; q++) {   // remember each hidden facet's blocker
+                        const int jb = __shfl_sync(kFull, jbit, q * s2);
+                        const int nb = __shfl_sync(kFull, myblk, q * s2);
+                        const bool vis = __shfl_sync(kFull, gvis, q * s2);
+                        if (lane == jb && !vis && nb >= 0) prev_blk = nb;
+                    }
+                }
                 for (int q = 0; q < cnt; q++) fm &= fm - 1;
             } else {
                 const int jbit = __ffs(fm) - 1;
                 fm &= fm - 1;
                 const int jlocal = 32 * c + jbit;
-                const Leaf Lf = load_leaf(g.leaf, D.facet0 + jlocal);
-                const float dirx = (float)(2 * Lf.ox + Lf.ux + Lf.vx - 2 * x);
-                const float diry = (float)(2 * Lf.oy + Lf.uy + Lf.vy - 2 * y);
-                const float dirz = (float)(2 * Lf.oz + Lf.uz + Lf.vz - 2 * z);
+                const int tb = __shfl_sync(kFull, prev_blk, jbit);
+                int last = -1;
+                bool vis = false;
                 for (int b0 = 0; b0 < s2; b0 += 32) {
                     const int b = b0 + lane;
-                    const bool mine = b < s2;
-                    const int sidx = D.sample0 + jlocal * s2 + b;
-                    int qx = 0, qy = 0, qz = 0;
-                    if (mine) { qx = __ldg(g.sx + sidx); qy = __ldg(g.sy + sidx); qz = __ldg(g.sz + sidx); }
-                    unsigned alive = __ballot_sync(kFull, mine);
-                    wc.segments += mine;
-                    const Seg sg = make_seg(x, y, z, qx, qy, qz);
-                    alive = occlude<CACHE>(sg, alive, g.nodes, g.leaf, D.root, dirx, diry, dirz,
-                                           budget, err, wc, leaf, cache);
+                    int myblk;
+                    const unsigned alive = table_packet<CACHE>(
+                        g, D, b < s2, D.sample0 + jlocal * s2 + b, D.facet0 + jlocal, x, y, z,
+                        tb, err, wc, leaf, cache, myblk);
                     if (alive) {
-                        word |= 1u << jbit;
+                        vis = true;
                         break;
                     }
+                    last = __shfl_sync(kFull, myblk, 0);
                 }
+                if (vis) word |= 1u << jbit;
+                else if (CACHE && lane == jbit && last >= 0) prev_blk = last;
             }
         }
         if (lane == 0) row[c] = word;
@@ -162,15 +221,17 @@ __device__ __forceinline__ void los_item(const DevScenes &g, long long chunk, in
     const float dirx = (float)__shfl_sync(kFull, sg.dx, lead);
     const float diry = (float)__shfl_sync(kFull, sg.dy, lead);
     const float dirz = (float)__shfl_sync(kFull, sg.dz, lead);
+    int myblk = -1;
     if (alive)
         alive = occlude<CACHE>(sg, alive, g.nodes, g.leaf, D.root, dirx, diry, dirz, 4 * D.n + 16,
-                               err, wc, leaf, cache);
+                               err, wc, leaf, cache, myblk);
     if (valid) D.los[t] = (uint8_t)((ok && same) || ((alive >> lane) & 1u));
 }
 
-// Items [0, 2 * total_snap) are table rows; items after them are LoS chunks.
+// Items [0, total_items) are table tiles; the next total_los_chunks are LoS.
 template <bool PERSIST, bool CACHE, class LeafFn>
-__global__ void k_table(DevScenes g, long long total_snap, long long total_items, int tile,
+__global__ void __launch_bounds__(kTravThreads, IVM_MIN_BLOCKS)
+k_table(DevScenes g, long long total_items, long long all_items, int TT,
                         const int *rep, unsigned long long *work, unsigned long long *ctr,
                         int *err)
 {
@@ -178,22 +239,20 @@ __global__ void k_table(DevScenes g, long long total_snap, long long total_items
     LeafFn leaf;
     OccluderCache cache;
     const int lane = threadIdx.x & 31;
-    const long long rows = 2 * total_snap;
     auto run = [&](long long it) {
-        if (it < rows) table_item<CACHE>(g, it, rep, err, wc, leaf, cache);
-        else los_item<CACHE>(g, it - rows, err, wc, leaf, cache);
+        if (it < total_items) table_tile<CACHE>(g, it, TT, rep, err, wc, leaf, cache);
+        else los_item<CACHE>(g, it - total_items, err, wc, leaf, cache);
     };
     if (!PERSIST) {
         long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-        if (w < total_items) run(w);
+        if (w < all_items) run(w);
     } else {
         for (;;) {
             unsigned long long base = 0;
-            if (lane == 0) base = atomicAdd(work, (unsigned long long)tile);
+            if (lane == 0) base = atomicAdd(work, 1ull);
             base = __shfl_sync(kFull, base, 0);
-            if ((long long)base >= total_items) break;
-            long long end = min((long long)base + tile, total_items);
-            for (long long it = (long long)base; it < end; it++) run(it);
+            if ((long long)base >= all_items) break;
+            run((long long)base);
         }
     }
     flush_counters(wc, ctr);
@@ -259,7 +318,7 @@ __global__ void k_copy_rows(DevScenes g, long long total_snap, const int *rep,
 // ------------------------------------------------------------ launchers
 
 template <bool PERSIST, bool CACHE, class LeafFn>
-static void launch_one(const DevScenes &g, long long total_snap, long long items,
+static void launch_one(const DevScenes &g, long long items, long long all, int TT,
                        const LaunchCfg &cfg, const int *rep, unsigned long long *work,
                        unsigned long long *ctr, int *err, cudaStream_t st)
 {
@@ -270,44 +329,44 @@ static void launch_one(const DevScenes &g, long long total_snap, long long items
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, 0);
         int blocks = cfg.n_sm * (per_sm > 0 ? per_sm : 1);
         cudaMemsetAsync(work, 0, sizeof(unsigned long long), st);
-        kern<<<blocks, threads, 0, st>>>(g, total_snap, items, cfg.tile, rep, work, ctr, err);
+        kern<<<blocks, threads, 0, st>>>(g, items, all, TT, rep, work, ctr, err);
     } else {
-        long long blocks = (items + cfg.warps_per_block - 1) / cfg.warps_per_block;
-        kern<<<(unsigned)blocks, threads, 0, st>>>(g, total_snap, items, 1, rep, work, ctr, err);
+        long long blocks = (all + cfg.warps_per_block - 1) / cfg.warps_per_block;
+        kern<<<(unsigned)blocks, threads, 0, st>>>(g, items, all, TT, rep, work, ctr, err);
     }
 }
 
 template <class LeafFn>
-static void launch_leaf(const DevScenes &g, long long total_snap, long long items,
+static void launch_leaf(const DevScenes &g, long long items, long long all, int TT,
                         const LaunchCfg &cfg, const int *rep, unsigned long long *work,
                         unsigned long long *ctr, int *err, cudaStream_t st)
 {
     if (cfg.persistent) {
-        if (cfg.cache) launch_one<true, true, LeafFn>(g, total_snap, items, cfg, rep, work, ctr, err, st);
-        else launch_one<true, false, LeafFn>(g, total_snap, items, cfg, rep, work, ctr, err, st);
+        if (cfg.cache) launch_one<true, true, LeafFn>(g, items, all, TT, cfg, rep, work, ctr, err, st);
+        else launch_one<true, false, LeafFn>(g, items, all, TT, cfg, rep, work, ctr, err, st);
     } else {
-        if (cfg.cache) launch_one<false, true, LeafFn>(g, total_snap, items, cfg, rep, work, ctr, err, st);
-        else launch_one<false, false, LeafFn>(g, total_snap, items, cfg, rep, work, ctr, err, st);
+        if (cfg.cache) launch_one<false, true, LeafFn>(g, items, all, TT, cfg, rep, work, ctr, err, st);
+        else launch_one<false, false, LeafFn>(g, items, all, TT, cfg, rep, work, ctr, err, st);
     }
 }
 
-cudaError_t launch_table(const DevScenes &g, long long total_snap, long long total_los_chunks,
-                         const LaunchCfg &cfg, int *rep, unsigned long long *work,
-                         unsigned long long *ctr, int *err, cudaStream_t st)
+cudaError_t launch_table(const DevScenes &g, long long total_snap, long long total_items,
+                         long long total_los_chunks, int snap_tile, const LaunchCfg &cfg,
+                         int *rep, unsigned long long *work, unsigned long long *ctr, int *err,
+                         cudaStream_t st)
 {
-    const long long items = 2 * total_snap + total_los_chunks;
-    if (items == 0) return cudaSuccess;
+    const long long all = total_items + total_los_chunks;
+    if (all == 0) return cudaSuccess;
     int launched = 1;
     if (cfg.dedup) {
         k_runs<<<dim3(g.n_scenes, 2), 1024, 0, st>>>(g, rep);
         launched++;
     }
+    const int *r = cfg.dedup ? rep : nullptr;
     if (cfg.mode == IVM_MODE_EXACT)
-        launch_leaf<ExactLeaf>(g, total_snap, items, cfg, cfg.dedup ? rep : nullptr, work, ctr,
-                               err, st);
+        launch_leaf<ExactLeaf>(g, total_items, all, snap_tile, cfg, r, work, ctr, err, st);
     else
-        launch_leaf<FilteredLeaf>(g, total_snap, items, cfg, cfg.dedup ? rep : nullptr, work,
-                                  ctr, err, st);
+        launch_leaf<FilteredLeaf>(g, total_items, all, snap_tile, cfg, r, work, ctr, err, st);
     if (cfg.dedup && total_snap > 0) {
         long long warps = 2 * total_snap;
         k_copy_rows<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, st>>>(g, total_snap, rep, ctr);

@@ -84,16 +84,20 @@ __device__ __forceinline__ int orient_sign(int ax, int ay, int az, int bx, int b
 // half-planes of the parallelogram, projected along its normal's dominant
 // axis; bounds are kept as exact fractions.  Open segment meets the closed
 // facet iff lo <= hi, lo < 1 and hi > 0.
-static __device__ __noinline__ bool coplanar_hit(const Seg &s, const Leaf &L)
+// (Arguments by value: the segment and the facet stay in registers in the
+// caller; only this rare path pays for the call.)
+static __device__ __noinline__ bool coplanar_hit_v(int px, int py, int pz, int dx, int dy, int dz,
+                                                   int ox, int oy, int oz, int ux, int uy, int uz,
+                                                   int vx, int vy, int vz, int dom)
 {
-    int a0 = L.dom == 0 ? 1 : 0;
-    int a1 = L.dom == 2 ? 1 : 2;
+    int a0 = dom == 0 ? 1 : 0;
+    int a1 = dom == 2 ? 1 : 2;
     auto pick = [](int x, int y, int z, int a) { return a == 0 ? x : (a == 1 ? y : z); };
-    long long P0 = pick(s.px, s.py, s.pz, a0), P1 = pick(s.px, s.py, s.pz, a1);
-    long long D0 = pick(s.dx, s.dy, s.dz, a0), D1 = pick(s.dx, s.dy, s.dz, a1);
-    long long O0 = pick(L.ox, L.oy, L.oz, a0), O1 = pick(L.ox, L.oy, L.oz, a1);
-    long long U0 = pick(L.ux, L.uy, L.uz, a0), U1 = pick(L.ux, L.uy, L.uz, a1);
-    long long V0 = pick(L.vx, L.vy, L.vz, a0), V1 = pick(L.vx, L.vy, L.vz, a1);
+    long long P0 = pick(px, py, pz, a0), P1 = pick(px, py, pz, a1);
+    long long D0 = pick(dx, dy, dz, a0), D1 = pick(dx, dy, dz, a1);
+    long long O0 = pick(ox, oy, oz, a0), O1 = pick(ox, oy, oz, a1);
+    long long U0 = pick(ux, uy, uz, a0), U1 = pick(ux, uy, uz, a1);
+    long long V0 = pick(vx, vy, vz, a0), V1 = pick(vx, vy, vz, a1);
     int sig = sgn_ll(U0 * V1 - U1 * V0);      // != 0: the dominant normal component
     long long cx[4] = {O0, O0 + U0, O0 + U0 + V0, O0 + V0};
     long long cy[4] = {O1, O1 + U1, O1 + U1 + V1, O1 + V1};
@@ -112,6 +116,12 @@ static __device__ __noinline__ bool coplanar_hit(const Seg &s, const Leaf &L)
         }
     }
     return ((__int128)lon * hid <= (__int128)hin * lod) && (lon < lod) && (hin > 0);
+}
+
+__device__ __forceinline__ bool coplanar_hit(const Seg &s, const Leaf &L)
+{
+    return coplanar_hit_v(s.px, s.py, s.pz, s.dx, s.dy, s.dz, L.ox, L.oy, L.oz, L.ux, L.uy, L.uz,
+                          L.vx, L.vy, L.vz, L.dom);
 }
 
 // Exact: does the open segment s meet the closed facet L?
@@ -159,11 +169,20 @@ __device__ __forceinline__ Leaf load_leaf(const Leaf *leaves, int g)
 
 // ------------------------------------------------------------ packet walk
 
-// Per-lane test counts; summed over the warp once per task (flush_counters).
+// Per-lane test counts, summed over the warp and flushed once per kernel.
+// A lane does far fewer than 2^32 tests in one launch.
 struct WalkCounters {
-    unsigned long long node_tests = 0, leaf_tests = 0, undecided = 0, exact = 0, segments = 0,
-                       cache_hits = 0;
+    unsigned node_tests = 0, leaf_tests = 0, undecided = 0, exact = 0, segments = 0,
+             cache_hits = 0;
 };
+
+// Traversal kernels run 128-thread blocks; the minimum-blocks hint caps
+// registers so that more warps per scheduler hide the latency of the
+// dependent box-test chains.
+constexpr int kTravThreads = 128;
+#ifndef IVM_MIN_BLOCKS
+#define IVM_MIN_BLOCKS 4
+#endif
 
 __device__ __forceinline__ unsigned long long warp_sum(unsigned long long v)
 {
@@ -171,7 +190,7 @@ __device__ __forceinline__ unsigned long long warp_sum(unsigned long long v)
     return v;
 }
 
-__device__ __forceinline__ void flush_counters(WalkCounters &wc, unsigned long long *ctr)
+__device__ __forceinline__ void flush_counters(const WalkCounters &wc, unsigned long long *ctr)
 {
     unsigned long long a = warp_sum(wc.node_tests), b = warp_sum(wc.leaf_tests),
                        c = warp_sum(wc.undecided), d = warp_sum(wc.exact),
@@ -184,7 +203,6 @@ __device__ __forceinline__ void flush_counters(WalkCounters &wc, unsigned long l
         if (d) atomicAdd(ctr + C_EXACT_TESTS, d);
         if (e) atomicAdd(ctr + C_SEGMENTS, e);
     }
-    wc = WalkCounters();
 }
 
 // Walks the BVH for the packet.  Must be called by all 32 lanes with the
@@ -197,12 +215,13 @@ template <class LeafFn>
 __device__ __forceinline__ unsigned walk_packet(const Seg &s, unsigned alive, const Node *nodes,
                                                 const Leaf *leaves, int root, float dirx,
                                                 float diry, float dirz, int budget, int *err,
-                                                WalkCounters &wc, LeafFn leaf_hit, int &blocker)
+                                                WalkCounters &wc, LeafFn leaf_hit, int &blocker,
+                                                int &myblk)
 {
     const int lane = threadIdx.x & 31;
     int s0 = 0, s1 = 0, sp = 0;   // stack: entry k lives in lane k&31 of s0 / s1
     int node = root;
-    blocker = -1;
+    blocker = -1;                 // warp-uniform: the last facet that blocked any lane
     while (alive) {
         if (--budget < 0) {
             if (lane == 0) raise_error(err, IVM_ERR_TIMEOUT);
@@ -216,6 +235,7 @@ __device__ __forceinline__ unsigned walk_packet(const Seg &s, unsigned alive, co
             wc.leaf_tests += me;
             const unsigned hm = __ballot_sync(kFull, hit);
             if (hm) blocker = ~node;
+            if (hit) myblk = ~node;   // per lane: the facet that blocked this segment
             alive &= ~hm;
         } else {
             const float4 *np = reinterpret_cast<const float4 *>(nodes + node);
@@ -295,12 +315,13 @@ struct OccluderCache {
 };
 
 // Lanes of the packet left unblocked: cached occluders first (when `cache`),
-// then the BVH walk.  Same contract as walk_packet.
+// then the BVH walk.  Same contract as walk_packet; `myblk` receives, in each
+// lane that gets blocked, the facet that blocked it.
 template <bool CACHE, class LeafFn>
 __device__ __forceinline__ unsigned occlude(const Seg &s, unsigned alive, const Node *nodes,
                                             const Leaf *leaves, int root, float dirx, float diry,
                                             float dirz, int budget, int *err, WalkCounters &wc,
-                                            LeafFn leaf_hit, OccluderCache &cache)
+                                            LeafFn leaf_hit, OccluderCache &cache, int &myblk)
 {
     const int lane = threadIdx.x & 31;
     if (CACHE) {
@@ -314,6 +335,7 @@ __device__ __forceinline__ unsigned occlude(const Seg &s, unsigned alive, const 
             bool hit = me && leaf_hit(s, L, wc);
             wc.leaf_tests += me;
             wc.cache_hits += hit;
+            if (hit) myblk = g;
             const unsigned hm = __ballot_sync(kFull, hit);
             alive &= ~hm;
             if (hm && k > 0 && promote < 0) promote = g;
@@ -323,7 +345,7 @@ __device__ __forceinline__ unsigned occlude(const Seg &s, unsigned alive, const 
     }
     int blocker;
     alive = walk_packet(s, alive, nodes, leaves, root, dirx, diry, dirz, budget, err, wc,
-                        leaf_hit, blocker);
+                        leaf_hit, blocker, myblk);
     if (CACHE) cache.put(blocker);
     return alive;
 }

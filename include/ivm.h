@@ -93,8 +93,9 @@ typedef struct ivm_params {
     int32_t samples_per_side; /* s, 1..8 */
     int32_t max_order;        /* K for ivm_expand_image_tree, 0..8 */
     int32_t mode;             /* IVM_MODE_* */
-    int32_t tile;             /* pairs per work item (0 = autotuned / default) */
-    int32_t warps_per_block;  /* 0 = autotuned / default */
+    int32_t tile;             /* matrix: pairs per queue pop; table: consecutive
+                                 snapshots per work item (0 = default) */
+    int32_t warps_per_block;  /* 1..4 (0 = default 4) */
     int32_t flags;            /* IVM_FLAG_* */
 } ivm_params;
 

@@ -106,7 +106,7 @@ int check_params(const ivm_params *p)
     if (!p) return IVM_ERR_ARG;
     if (p->samples_per_side < 1 || p->samples_per_side > kMaxSamplesPerSide) return IVM_ERR_ARG;
     if (p->mode < IVM_MODE_EXACT || p->mode > IVM_MODE_LEARNED) return IVM_ERR_ARG;
-    if (p->tile < 0 || p->warps_per_block < 0 || p->warps_per_block > 16) return IVM_ERR_ARG;
+    if (p->tile < 0 || p->warps_per_block < 0 || p->warps_per_block > 4) return IVM_ERR_ARG;
     return IVM_OK;
 }
 

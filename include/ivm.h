@@ -174,6 +174,31 @@ int ivm_expand_image_tree(ivm_ctx *ctx, const uint32_t *matrix, const uint32_t *
 /* Message for an error code (static string). */
 const char *ivm_strerror(int code);
 
+/* Matrix build that allocates no memory (the paper has no counterpart).
+ * For callers that cannot allocate device memory during the call: code
+ * running inside an allocator or memory pool that forbids cudaMalloc,
+ * real-time loops that must not take the allocator's synchronisation, hosts
+ * that own all device memory.  Computes the same matrix as ivm_build_matrix
+ * for one scene, without a context: every scratch buffer lives in one fixed
+ * device array of the library (about 5 MB, held on every GPU that loads the
+ * library until the process exits).
+ *   facets  device pointer, n_facets records (1..IVM_NOALLOC_MAX_FACETS);
+ *   params  samples_per_side 1..IVM_NOALLOC_MAX_SAMPLES_PER_SIDE, mode and
+ *           the PERSISTENT / OCCLUDER_CACHE flags as for ivm_build_matrix;
+ *   matrix  device pointer, [n_facets][W] words, written as ivm_build_matrix;
+ *   cuda_stream  cudaStream_t of the current device (NULL: legacy stream).
+ * Runs on the current device.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress); make that first call
+ * before any stream capture.  Calls share the array: each call clears what
+ * must start at zero, and calls that overlap on the GPU race on it.  It
+ * synchronises the stream before returning.  Errors: IVM_ERR_ARG (null
+ * pointer, or n_facets / samples_per_side above the limits), IVM_ERR_RANGE,
+ * IVM_ERR_TIMEOUT, IVM_ERR_INTERNAL, IVM_ERR_CUDA. */
+#define IVM_NOALLOC_MAX_FACETS 1024
+#define IVM_NOALLOC_MAX_SAMPLES_PER_SIDE 5
+int ivm_build_matrix_noalloc(const ivm_facet *facets, int32_t n_facets, const ivm_params *params,
+                             uint32_t *matrix, void *cuda_stream);
+
 /* Diagnostic, not from the paper: number of CUDA kernels this library has
  * launched in this process so far (all contexts and threads).  Lets a caller
  * count the launches of a timed region without a profiler. */

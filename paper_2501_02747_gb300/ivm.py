@@ -73,7 +73,22 @@ SIGNATURES = {
                                ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
     "ivm_strerror": ([ctypes.c_int], ctypes.c_char_p),
     "ivm_kernel_launches": ([], ctypes.c_uint64),
+    "ivm_build_matrix_noalloc": ([_VP, ctypes.c_int32, ctypes.POINTER(ivm_params), _VP, _VP],
+                                 ctypes.c_int),
 }
+
+NOALLOC_MAX_FACETS, NOALLOC_MAX_SAMPLES_PER_SIDE = 1024, 5
+
+
+def ivm_build_matrix_noalloc(facets_dev, s, matrix_dev, stream, mode=IVM_MODE_EXACT, flags=0):
+    """Matrix of one scene through the allocation-free entry point.
+
+    facets_dev (int32 [N][10]) and matrix_dev (int32 [N][W]) must be device
+    tensors of the current device; returns the C return code."""
+    p = _params(s, 0, mode, 0, 0, flags)
+    return lib().ivm_build_matrix_noalloc(_addr(facets_dev), int(facets_dev.shape[0]),
+                                          ctypes.byref(p), _addr(matrix_dev),
+                                          _VP(stream.cuda_stream))
 
 
 def kernel_launches() -> int:

@@ -233,14 +233,23 @@ def run_ours(args, ws, rank, local):
         "plain": dict(mode=ivm.IVM_MODE_EXACT, flags=0),
         "fast": dict(mode=ivm.IVM_MODE_FILTERED,
                      flags=ivm.IVM_FLAG_PERSISTENT | ivm.IVM_FLAG_OCCLUDER_CACHE
-                     | ivm.IVM_FLAG_DEDUP_SOURCES),
+                     | ivm.IVM_FLAG_DEDUP_SOURCES | ivm.IVM_FLAG_GRAPH),
     }
 
-    def step(form, fac, tx, rx, M, T, L, summ):
+    def step(form, fac, tx, rx, M, T, L, summ, marks=None):
+        """The three calls; `marks` (4 CUDA events) bracket them on the stream."""
         kw = forms[form]
+        if marks:
+            marks[0].record(stream)
         _, stm = ivm.ivm_build_matrix(ctx, fac, s, out=M, **kw)
+        if marks:
+            marks[1].record(stream)
         _, stt = ivm.ivm_build_table(ctx, fac, s, tx, rx, out=(T, L), **kw)
+        if marks:
+            marks[2].record(stream)
         ivm.ivm_expand_image_tree(ctx, M, T, L, N, K, summary=summ)
+        if marks:
+            marks[3].record(stream)
         return stm, stt
 
     if args.profile:
@@ -274,16 +283,16 @@ def run_ours(args, ws, rank, local):
         launches0 = ivm.kernel_launches()
         times, kern = [], {"matrix": 0.0, "table": 0.0}
         ops, node_tests, leaf_tests = {"matrix": 0, "table": 0}, 0, 0
+        calls = {"matrix": 0.0, "table": 0.0, "tree": 0.0}
         stats = None
         for _ in range(args.steps):
             flush.zero_()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            stm, stt = step(form, facets_d, tx_d, rx_d, M_d, T_d, L_d, summ_d)
-            e1.record(stream)
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+            stm, stt = step(form, facets_d, tx_d, rx_d, M_d, T_d, L_d, summ_d, marks=ev)
             torch.cuda.synchronize()
-            times.append(e0.elapsed_time(e1))
+            times.append(ev[0].elapsed_time(ev[3]))
+            for k, name in enumerate(("matrix", "table", "tree")):
+                calls[name] += ev[k].elapsed_time(ev[k + 1]) / args.steps
             kern["matrix"] += stm.ms_traverse
             kern["table"] += stt.ms_traverse
             for name, st in (("matrix", stm), ("table", stt)):
@@ -295,12 +304,12 @@ def run_ours(args, ws, rank, local):
         torch.cuda.synchronize()
         barrier(ws)
         ms = max_over_ranks(ws, sum(times)) / args.steps
-        return ms, kern, ops, launches, stats, times
+        return ms, kern, ops, launches, stats, calls
 
     clocks = Clocks(local)
-    ms_plain, kern_plain, ops_plain, _, stats_plain, _ = timed("plain")
+    ms_plain, kern_plain, ops_plain, _, stats_plain, calls_plain = timed("plain")
     clocks.start()
-    ms_fast, kern_fast, ops_fast, launches, stats_fast, times = timed("fast")
+    ms_fast, kern_fast, ops_fast, launches, stats_fast, calls_fast = timed("fast")
     clk = clocks.stop()
 
     # parity of the two forms on this step's outputs (cheap, outside timing)
@@ -317,13 +326,15 @@ def run_ours(args, ws, rank, local):
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "form": "fast: FP32 filter + exact fallback, "
                    "persistent work queue, occluder cache, one row per run of equal "
-                   "source positions", "l2": "flushed between steps (512 MB write)",
+                   "source positions, CUDA-graph replay of each call",
+                   "l2": "flushed between steps (512 MB write)",
                    "facets": N, "snapshots": S, "samples_per_side": s, "max_order": K,
                    "pair_tests_per_step": units},
         "snapshot_tables_per_s": ws * S / (ms_fast / 1e3),
         "plain": {"ms_per_step": ms_plain, "value": ws * units / (ms_plain / 1e3),
                   "form": "exact int64/int128 facet tests, one warp per work item"},
         "speedup_vs_plain": ms_plain / ms_fast,
+        "ms_per_call": {"fast": calls_fast, "plain": calls_plain},
         "forms_bit_identical": forms_agree,
         "gpu_launches": launches,
         "clocks": clk,

@@ -1,5 +1,14 @@
 // ivm_api.cu -- the C ABI declared in include/ivm.h: context, scratch arena,
 // host/device argument staging, and the launch sequences of the three calls.
+//
+// Each build call runs in four stages: plan (lay out the scenes and grow the
+// arena -- the only place that allocates), enqueue (copies, memsets and
+// kernels on the context's stream), execute (directly, or by replaying a
+// CUDA graph captured from the enqueue stage), finalize (one
+// synchronisation, the device error word, copies back to host buffers,
+// stats).  The persistent form enqueues without any host synchronisation:
+// the matrix kernel reads the candidate-pair count from device memory and
+// the ingest range check is reported at the end.
 #include <atomic>
 #include <cstdio>
 #include <cstring>
@@ -20,7 +29,7 @@ enum Slot {
     S_FACETS, S_DESC, S_LEAF, S_FSCENE, S_BOX, S_SX, S_SY, S_SZ, S_KEYS, S_SORTED, S_BOUNDS,
     S_ORDER, S_NODES, S_PARENT, S_VISITS, S_PAIRS, S_OUT, S_TX, S_RX, S_LOS, S_REP,
     S_T_MAT, S_T_TAB, S_T_LOS, S_T_SUM, S_T_DEG, S_T_ROW, S_T_COL, S_T_WT, S_T_XA, S_T_XB,
-    S_T_CNT, S_T_OFF, S_T_BS, S_T_BO, S_T_PATHS,
+    S_T_CNT, S_T_OFF, S_T_BS, S_T_BO, S_T_PATHS, S_T_FLAG, S_T_EXCL, S_T_RUN, S_T_START,
     S_COUNT
 };
 
@@ -29,6 +38,20 @@ struct Buf {
     size_t cap = 0;
 };
 
+// A captured launch sequence, replayed while the call's shape and buffers
+// are unchanged.
+struct GraphEntry {
+    std::vector<unsigned long long> key;
+    cudaGraphExec_t exec = nullptr;
+    SceneDesc *h_desc = nullptr;   // pinned copy the graph's first node reads
+    unsigned long long gen = 0;    // arena generation at capture
+    unsigned long long last_use = 0;
+    int kernels = 0;               // kernels per replay (launch accounting)
+};
+
+constexpr int kMaxGraphs = 8;
+constexpr long long kDevCountMaxPairs = 1LL << 31;   // upper-bound pair list cap (16 GB)
+
 }  // namespace
 
 struct ivm_ctx {
@@ -36,12 +59,16 @@ struct ivm_ctx {
     cudaStream_t stream = nullptr;
     int n_sm = 0;
     Buf buf[S_COUNT];
+    unsigned long long arena_gen = 1;     // bumps whenever a buffer moves
     int *d_err = nullptr;                 // device error word
     unsigned long long *d_ctr = nullptr;  // C_COUNT_ counters
-    unsigned long long *d_misc = nullptr; // [0] count, [1] cursor, [2] work queue
+    unsigned long long *d_misc = nullptr; // [0] pair count, [1] cursor, [2] work queue
     int *h_err = nullptr;
     unsigned long long *h_ctr = nullptr, *h_misc = nullptr;
     cudaEvent_t ev[8] = {};
+    std::vector<GraphEntry> graphs;
+    unsigned long long uses = 0;
+    cudaStream_t cap = nullptr;           // private stream used only for capture
 };
 
 namespace {
@@ -80,6 +107,7 @@ int ensure(ivm_ctx *c, int slot, size_t bytes)
     size_t want = bytes + bytes / 4 + 256;
     CK(cudaMalloc(&b.p, want));
     b.cap = want;
+    c->arena_gen++;
     return IVM_OK;
 }
 
@@ -114,7 +142,8 @@ LaunchCfg launch_cfg(const ivm_ctx *c, const ivm_params *p)
 {
     LaunchCfg L;
     L.mode = p->mode == IVM_MODE_EXACT ? IVM_MODE_EXACT : IVM_MODE_FILTERED;
-    L.persistent = (p->flags & IVM_FLAG_PERSISTENT) != 0;
+    // graph replay needs the synchronisation-free (persistent) sequence
+    L.persistent = (p->flags & (IVM_FLAG_PERSISTENT | IVM_FLAG_GRAPH)) != 0;
     L.warps_per_block = p->warps_per_block > 0 ? p->warps_per_block : 4;
     L.tile = p->tile > 0 ? p->tile : (L.persistent ? 4 : 1);
     L.n_sm = c->n_sm;
@@ -123,10 +152,9 @@ LaunchCfg launch_cfg(const ivm_ctx *c, const ivm_params *p)
     return L;
 }
 
-// Copies the scenes' facets into the arena, lays out the per-scene
-// descriptors, and points the geometry arrays into the arena.
-int setup_geometry(ivm_ctx *c, const ivm_scene *scenes, int n_scenes, int s, DevScenes &g,
-                   std::vector<SceneDesc> &hd)
+// Lays out the per-scene descriptors and grows the geometry buffers.
+int plan_geometry(ivm_ctx *c, const ivm_scene *scenes, int n_scenes, int s, DevScenes &g,
+                  std::vector<SceneDesc> &hd)
 {
     if (!scenes || n_scenes < 1) return IVM_ERR_ARG;
     hd.assign(n_scenes, SceneDesc());
@@ -166,17 +194,19 @@ int setup_geometry(ivm_ctx *c, const ivm_scene *scenes, int n_scenes, int s, Dev
     if ((r = ensure(c, S_NODES, sizeof(Node) * (nodes > 0 ? nodes : 1)))) return r;
     if ((r = ensure(c, S_PARENT, sizeof(int) * (facets + nodes)))) return r;
     if ((r = ensure(c, S_VISITS, sizeof(int) * (nodes > 0 ? nodes : 1)))) return r;
-    ivm_facet *df = ptr<ivm_facet>(c, S_FACETS);
-    for (int k = 0; k < n_scenes; k++)
-        CK(cudaMemcpyAsync(df + hd[k].facet0, scenes[k].facets,
-                           sizeof(ivm_facet) * scenes[k].n_facets, cudaMemcpyDefault, c->stream));
     g.n_scenes = n_scenes;
     g.total_facets = (int)facets;
     g.total_nodes = (int)nodes;
     g.total_samples = (int)samples;
     g.max_n = (int)maxn;
+    return IVM_OK;
+}
+
+// Arena pointers (call after every ensure of the call is done).
+void bind_geometry(ivm_ctx *c, DevScenes &g)
+{
     g.desc = ptr<SceneDesc>(c, S_DESC);
-    g.facets = df;
+    g.facets = ptr<ivm_facet>(c, S_FACETS);
     g.leaf = ptr<Leaf>(c, S_LEAF);
     g.fscene = ptr<int>(c, S_FSCENE);
     g.box = ptr<int>(c, S_BOX);
@@ -190,7 +220,19 @@ int setup_geometry(ivm_ctx *c, const ivm_scene *scenes, int n_scenes, int s, Dev
     g.nodes = ptr<Node>(c, S_NODES);
     g.parent = ptr<int>(c, S_PARENT);
     g.visits = ptr<int>(c, S_VISITS);
-    return IVM_OK;
+}
+
+// Phase events.  Inside a capture they are recorded as "external" event
+// nodes, so that a replay records them too (a plain record inside a capture
+// only orders the graph's nodes); the flag is refused outside a capture.
+cudaError_t record(ivm_ctx *c, int i)
+{
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(c->stream, &cs);
+    if (e != cudaSuccess) return e;
+    if (cs == cudaStreamCaptureStatusActive)
+        return cudaEventRecordWithFlags(c->ev[i], c->stream, cudaEventRecordExternal);
+    return cudaEventRecord(c->ev[i], c->stream);
 }
 
 int read_error(ivm_ctx *c)
@@ -200,22 +242,28 @@ int read_error(ivm_ctx *c)
     return *c->h_err;
 }
 
-int reset_counters(ivm_ctx *c)
+// Facet copies, descriptors, zeroed counters, ingest and BVH.  With
+// `check` the ingest range check is read back before the BVH is built.
+int enqueue_geometry(ivm_ctx *c, const DevScenes &g, const ivm_scene *scenes,
+                     const std::vector<SceneDesc> &hd, const SceneDesc *desc_src, bool check)
 {
+    ivm_facet *df = ptr<ivm_facet>(c, S_FACETS);
+    for (int k = 0; k < g.n_scenes; k++)
+        CK(cudaMemcpyAsync(df + hd[k].facet0, scenes[k].facets,
+                           sizeof(ivm_facet) * scenes[k].n_facets, cudaMemcpyDefault, c->stream));
+    CK(cudaMemcpyAsync(g.desc, desc_src, sizeof(SceneDesc) * g.n_scenes, cudaMemcpyHostToDevice,
+                       c->stream));
     CK(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
     CK(cudaMemsetAsync(c->d_ctr, 0, sizeof(unsigned long long) * C_COUNT_, c->stream));
-    return IVM_OK;
-}
-
-// Ingest + BVH for a call's scenes; leaves the geometry on the device.
-int build_geometry(ivm_ctx *c, const DevScenes &g)
-{
+    CK(record(c, 0));
     CK(launch_ingest(g, c->d_err, c->stream));
-    int e = read_error(c);
-    if (e) return e;
-    CK(cudaEventRecord(c->ev[1], c->stream));
+    if (check) {
+        int e = read_error(c);
+        if (e) return e;
+    }
+    CK(record(c, 1));
     CK(launch_bvh(g, c->stream));
-    CK(cudaEventRecord(c->ev[2], c->stream));
+    CK(record(c, 2));
     return IVM_OK;
 }
 
@@ -251,6 +299,99 @@ int fill_stats(ivm_ctx *c, ivm_stats *st, unsigned long long pairs, int phases)
     st->ms_traverse = elapsed(c->ev[phases >= 3 ? 3 : 2], c->ev[4]);
     st->ms_total = elapsed(c->ev[0], c->ev[4]);
     return IVM_OK;
+}
+
+// ------------------------------------------------------------------ graphs
+
+void drop_graph(GraphEntry &e)
+{
+    if (e.exec) cudaGraphExecDestroy(e.exec);
+    if (e.h_desc) cudaFreeHost(e.h_desc);
+    e = GraphEntry();
+}
+
+GraphEntry *find_graph(ivm_ctx *c, const std::vector<unsigned long long> &key)
+{
+    for (auto &e : c->graphs)
+        if (e.exec && e.gen == c->arena_gen && e.key == key) {
+            e.last_use = ++c->uses;
+            return &e;
+        }
+    return nullptr;
+}
+
+// Captures `enqueue` (a callable returning an IVM code) into a new entry.
+template <class F>
+int capture_graph(ivm_ctx *c, const std::vector<unsigned long long> &key, size_t desc_bytes,
+                  const SceneDesc *desc, F &&enqueue, GraphEntry **out)
+{
+    // evict stale entries, then the least recently used one if full
+    for (auto &e : c->graphs)
+        if (e.exec && e.gen != c->arena_gen) drop_graph(e);
+    GraphEntry *slot = nullptr;
+    for (auto &e : c->graphs)
+        if (!e.exec) { slot = &e; break; }
+    if (!slot) {
+        if ((int)c->graphs.size() < kMaxGraphs) {
+            c->graphs.emplace_back();
+            slot = &c->graphs.back();
+        } else {
+            slot = &c->graphs[0];
+            for (auto &e : c->graphs)
+                if (e.last_use < slot->last_use) slot = &e;
+            drop_graph(*slot);
+        }
+    }
+    CK(cudaMallocHost(&slot->h_desc, desc_bytes));
+    memcpy(slot->h_desc, desc, desc_bytes);
+    // The caller's stream may be the legacy default stream, which cannot be
+    // captured: record on a private stream; the graph is launched on the
+    // caller's stream afterwards.
+    if (!c->cap) CK(cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));
+    const unsigned long long l0 = g_launches.load();
+    cudaStream_t user = c->stream;
+    c->stream = c->cap;
+    cudaError_t eb = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
+    int r = eb == cudaSuccess ? enqueue(slot->h_desc) : IVM_ERR_CUDA;
+    cudaGraph_t graph = nullptr;
+    cudaError_t ec = eb == cudaSuccess ? cudaStreamEndCapture(c->stream, &graph) : eb;
+    c->stream = user;
+    if (r || ec != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        drop_graph(*slot);
+        return r ? r : IVM_ERR_CUDA;
+    }
+    cudaError_t ei = cudaGraphInstantiate(&slot->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ei != cudaSuccess) {
+        cudaGetLastError();
+        drop_graph(*slot);
+        return IVM_ERR_CUDA;
+    }
+    slot->kernels = (int)(g_launches.load() - l0);
+    g_launches.fetch_sub((unsigned long long)slot->kernels);   // counted when replayed
+    slot->key = key;
+    slot->gen = c->arena_gen;
+    slot->last_use = ++c->uses;
+    *out = slot;
+    return IVM_OK;
+}
+
+int replay(ivm_ctx *c, GraphEntry *e)
+{
+    CK(cudaGraphLaunch(e->exec, c->stream));
+    note_launches(e->kernels);
+    return IVM_OK;
+}
+
+void key_params(std::vector<unsigned long long> &k, const ivm_params *p)
+{
+    k.push_back((unsigned long long)p->samples_per_side);
+    k.push_back((unsigned long long)p->mode);
+    k.push_back((unsigned long long)p->tile);
+    k.push_back((unsigned long long)p->warps_per_block);
+    k.push_back((unsigned long long)p->flags);
 }
 
 }  // namespace
@@ -303,6 +444,8 @@ extern "C" int ivm_destroy(ivm_ctx *c)
     if (!c) return IVM_OK;
     DeviceGuard dg(c->device);
     cudaStreamSynchronize(c->stream);
+    for (auto &e : c->graphs) drop_graph(e);
+    if (c->cap) cudaStreamDestroy(c->cap);
     for (auto &b : c->buf)
         if (b.p) cudaFree(b.p);
     cudaFree(c->d_err);
@@ -327,47 +470,78 @@ extern "C" int ivm_build_matrix(ivm_ctx *c, const ivm_scene *scenes, int32_t n_s
     DeviceGuard dg(c->device);
     DevScenes g;
     std::vector<SceneDesc> hd;
-    if ((r = setup_geometry(c, scenes, n_scenes, params->samples_per_side, g, hd))) return r;
-    // outputs: device pointers are written in place; host ones go via the arena
+    // ---- plan
+    if ((r = plan_geometry(c, scenes, n_scenes, params->samples_per_side, g, hd))) return r;
     std::vector<char> on_host(n_scenes);
+    bool all_device = true;
     size_t host_words = 0;
+    long long upper = 0;
+    unsigned long long pairs_total = 0;
     for (int k = 0; k < n_scenes; k++) {
         if (!matrix[k]) return IVM_ERR_ARG;
         on_host[k] = !is_device(matrix[k]);
+        all_device &= !on_host[k] && is_device(scenes[k].facets);
         if (on_host[k]) host_words += (size_t)hd[k].n * hd[k].W;
-    }
-    if ((r = ensure(c, S_OUT, sizeof(uint32_t) * host_words))) return r;
-    size_t off = 0;
-    unsigned long long pairs_total = 0;
-    for (int k = 0; k < n_scenes; k++) {
-        size_t nw = (size_t)hd[k].n * hd[k].W;
-        hd[k].matrix = on_host[k] ? ptr<uint32_t>(c, S_OUT) + off : matrix[k];
-        if (on_host[k]) off += nw;
+        upper += (long long)hd[k].n * (hd[k].n - 1) / 2;
         pairs_total += (unsigned long long)hd[k].n * hd[k].n;
     }
-    CK(cudaMemcpyAsync(g.desc, hd.data(), sizeof(SceneDesc) * n_scenes, cudaMemcpyHostToDevice,
-                       c->stream));
-    if ((r = reset_counters(c))) return r;
-    CK(cudaEventRecord(c->ev[0], c->stream));
-    if ((r = build_geometry(c, g))) return r;
-    // facing screen -> candidate pair list
-    CK(cudaMemsetAsync(c->d_misc, 0, sizeof(unsigned long long) * 2, c->stream));
-    CK(launch_screen_count(g, hd.data(), c->d_misc, c->stream));
-    CK(cudaMemcpyAsync(c->h_misc, c->d_misc, sizeof(unsigned long long), cudaMemcpyDeviceToHost,
-                       c->stream));
-    CK(cudaStreamSynchronize(c->stream));
-    const unsigned long long npairs = c->h_misc[0];
-    if ((r = ensure(c, S_PAIRS, sizeof(int2) * npairs))) return r;
-    CK(launch_screen_emit(g, hd.data(), ptr<int2>(c, S_PAIRS), c->d_misc + 1, npairs, c->stream));
-    CK(cudaMemcpyAsync(c->d_ctr + C_CAND_PAIRS, c->d_misc, sizeof(unsigned long long),
-                       cudaMemcpyDeviceToDevice, c->stream));
-    CK(cudaEventRecord(c->ev[3], c->stream));
-    for (int k = 0; k < n_scenes; k++)
-        CK(cudaMemsetAsync(hd[k].matrix, 0, sizeof(uint32_t) * hd[k].n * hd[k].W, c->stream));
-    const LaunchCfg cfg = launch_cfg(c, params);
-    CK(launch_matrix(g, ptr<int2>(c, S_PAIRS), npairs, cfg, c->d_misc + 2, c->d_ctr, c->d_err,
-                     c->stream));
-    CK(cudaEventRecord(c->ev[4], c->stream));
+    const LaunchCfg cfg0 = launch_cfg(c, params);
+    const bool dev_count = cfg0.persistent && upper <= kDevCountMaxPairs;
+    const bool use_graph = (params->flags & IVM_FLAG_GRAPH) && dev_count && all_device;
+    if ((r = ensure(c, S_OUT, sizeof(uint32_t) * host_words))) return r;
+    if (dev_count && (r = ensure(c, S_PAIRS, sizeof(int2) * (size_t)upper))) return r;
+    size_t off = 0;
+    for (int k = 0; k < n_scenes; k++) {
+        hd[k].matrix = on_host[k] ? ptr<uint32_t>(c, S_OUT) + off : matrix[k];
+        if (on_host[k]) off += (size_t)hd[k].n * hd[k].W;
+    }
+    // ---- enqueue
+    auto enqueue = [&](const SceneDesc *desc_src) -> int {
+        int e;
+        bind_geometry(c, g);
+        if ((e = enqueue_geometry(c, g, scenes, hd, desc_src, !dev_count))) return e;
+        CK(cudaMemsetAsync(c->d_misc, 0, sizeof(unsigned long long) * 2, c->stream));
+        CK(launch_screen_count(g, hd.data(), c->d_misc, c->stream));
+        unsigned long long npairs = (unsigned long long)upper;
+        if (!dev_count) {   // size the pair list from the count
+            CK(cudaMemcpyAsync(c->h_misc, c->d_misc, sizeof(unsigned long long),
+                               cudaMemcpyDeviceToHost, c->stream));
+            CK(cudaStreamSynchronize(c->stream));
+            npairs = c->h_misc[0];
+            if ((e = ensure(c, S_PAIRS, sizeof(int2) * npairs))) return e;
+        }
+        CK(launch_screen_emit(g, hd.data(), ptr<int2>(c, S_PAIRS), c->d_misc + 1, npairs,
+                              c->stream));
+        CK(cudaMemcpyAsync(c->d_ctr + C_CAND_PAIRS, c->d_misc, sizeof(unsigned long long),
+                           cudaMemcpyDeviceToDevice, c->stream));
+        CK(record(c, 3));
+        for (int k = 0; k < n_scenes; k++)
+            CK(cudaMemsetAsync(hd[k].matrix, 0, sizeof(uint32_t) * hd[k].n * hd[k].W, c->stream));
+        LaunchCfg cfg = cfg0;
+        cfg.count_dev = dev_count ? c->d_misc : nullptr;
+        CK(launch_matrix(g, ptr<int2>(c, S_PAIRS), npairs, cfg, c->d_misc + 2, c->d_ctr,
+                         c->d_err, c->stream));
+        CK(record(c, 4));
+        return IVM_OK;
+    };
+    // ---- execute
+    if (use_graph) {
+        std::vector<unsigned long long> key = {0ull, (unsigned long long)n_scenes};
+        key_params(key, params);
+        for (int k = 0; k < n_scenes; k++) {
+            key.push_back((unsigned long long)(uintptr_t)scenes[k].facets);
+            key.push_back((unsigned long long)scenes[k].n_facets);
+            key.push_back((unsigned long long)(uintptr_t)matrix[k]);
+        }
+        GraphEntry *ge = find_graph(c, key);
+        if (!ge && (r = capture_graph(c, key, sizeof(SceneDesc) * n_scenes, hd.data(), enqueue,
+                                      &ge)))
+            return r;
+        if ((r = replay(c, ge))) return r;
+    } else {
+        if ((r = enqueue(hd.data()))) return r;
+    }
+    // ---- finalize
     if ((r = read_error(c))) return r;
     for (int k = 0; k < n_scenes; k++)
         if (on_host[k])
@@ -388,12 +562,14 @@ extern "C" int ivm_build_table(ivm_ctx *c, const ivm_scene *scenes, int32_t n_sc
     DeviceGuard dg(c->device);
     DevScenes g;
     std::vector<SceneDesc> hd;
-    if ((r = setup_geometry(c, scenes, n_scenes, params->samples_per_side, g, hd))) return r;
+    // ---- plan
+    if ((r = plan_geometry(c, scenes, n_scenes, params->samples_per_side, g, hd))) return r;
     long long snaps = 0, chunks = 0, items = 0;
     const int snap_tile = params->tile > 0 ? params->tile : 16;
     size_t host_tab = 0, host_los = 0, pos_tx = 0, pos_rx = 0;
     std::vector<char> tab_host(n_scenes), los_host(n_scenes), tx_host(n_scenes),
         rx_host(n_scenes);
+    bool all_device = true;
     for (int k = 0; k < n_scenes; k++) {
         if (n_snap[k] < 0) return IVM_ERR_ARG;
         if (n_snap[k] > 0 && (!table[k] || !los[k] || !tx[k] || !rx[k])) return IVM_ERR_ARG;
@@ -405,22 +581,29 @@ extern "C" int ivm_build_table(ivm_ctx *c, const ivm_scene *scenes, int32_t n_sc
         snaps += n_snap[k];
         chunks += (n_snap[k] + 31) / 32;
         items += 2LL * hd[k].W * hd[k].ntiles;
+        all_device &= is_device(scenes[k].facets);
         const size_t S = (size_t)n_snap[k];
         if (S == 0) continue;
         tab_host[k] = !is_device(table[k]);
         los_host[k] = !is_device(los[k]);
         tx_host[k] = !is_device(tx[k]);
         rx_host[k] = !is_device(rx[k]);
+        all_device &= !tab_host[k] && !los_host[k] && !tx_host[k] && !rx_host[k];
         if (tab_host[k]) host_tab += S * 2 * hd[k].W;
         if (los_host[k]) host_los += S;
         if (tx_host[k]) pos_tx += 3 * S;
         if (rx_host[k]) pos_rx += 3 * S;
     }
+    const LaunchCfg cfg = launch_cfg(c, params);
+    const bool sync_free = cfg.persistent;
+    const bool use_graph = (params->flags & IVM_FLAG_GRAPH) && all_device;
     if ((r = ensure(c, S_OUT, sizeof(uint32_t) * host_tab))) return r;
     if ((r = ensure(c, S_LOS, host_los))) return r;
     if ((r = ensure(c, S_TX, sizeof(int) * pos_tx))) return r;
     if ((r = ensure(c, S_RX, sizeof(int) * pos_rx))) return r;
+    if (cfg.dedup && (r = ensure(c, S_REP, sizeof(int) * 2 * (size_t)snaps))) return r;
     size_t o_tab = 0, o_los = 0, o_tx = 0, o_rx = 0;
+    std::vector<int> tx_off(n_scenes, -1), rx_off(n_scenes, -1);
     for (int k = 0; k < n_scenes; k++) {
         const size_t S = (size_t)n_snap[k];
         if (S == 0) continue;
@@ -429,32 +612,61 @@ extern "C" int ivm_build_table(ivm_ctx *c, const ivm_scene *scenes, int32_t n_sc
         hd[k].los = los_host[k] ? ptr<uint8_t>(c, S_LOS) + o_los : los[k];
         if (los_host[k]) o_los += S;
         if (tx_host[k]) {
-            int *d = ptr<int>(c, S_TX) + o_tx;
-            CK(cudaMemcpyAsync(d, tx[k], sizeof(int) * 3 * S, cudaMemcpyHostToDevice, c->stream));
-            hd[k].tx = d;
+            hd[k].tx = ptr<int>(c, S_TX) + o_tx;
+            tx_off[k] = (int)o_tx;
             o_tx += 3 * S;
         } else {
             hd[k].tx = tx[k];
         }
         if (rx_host[k]) {
-            int *d = ptr<int>(c, S_RX) + o_rx;
-            CK(cudaMemcpyAsync(d, rx[k], sizeof(int) * 3 * S, cudaMemcpyHostToDevice, c->stream));
-            hd[k].rx = d;
+            hd[k].rx = ptr<int>(c, S_RX) + o_rx;
+            rx_off[k] = (int)o_rx;
             o_rx += 3 * S;
         } else {
             hd[k].rx = rx[k];
         }
     }
-    CK(cudaMemcpyAsync(g.desc, hd.data(), sizeof(SceneDesc) * n_scenes, cudaMemcpyHostToDevice,
-                       c->stream));
-    if ((r = reset_counters(c))) return r;
-    CK(cudaEventRecord(c->ev[0], c->stream));
-    if ((r = build_geometry(c, g))) return r;
-    const LaunchCfg cfg = launch_cfg(c, params);
-    if (cfg.dedup && (r = ensure(c, S_REP, sizeof(int) * 2 * (size_t)snaps))) return r;
-    CK(launch_table(g, snaps, items, chunks, snap_tile, cfg, ptr<int>(c, S_REP), c->d_misc + 2,
-                    c->d_ctr, c->d_err, c->stream));
-    CK(cudaEventRecord(c->ev[4], c->stream));
+    // ---- enqueue
+    auto enqueue = [&](const SceneDesc *desc_src) -> int {
+        int e;
+        bind_geometry(c, g);
+        for (int k = 0; k < n_scenes; k++) {
+            const size_t S = (size_t)n_snap[k];
+            if (tx_off[k] >= 0)
+                CK(cudaMemcpyAsync(ptr<int>(c, S_TX) + tx_off[k], tx[k], sizeof(int) * 3 * S,
+                                   cudaMemcpyHostToDevice, c->stream));
+            if (rx_off[k] >= 0)
+                CK(cudaMemcpyAsync(ptr<int>(c, S_RX) + rx_off[k], rx[k], sizeof(int) * 3 * S,
+                                   cudaMemcpyHostToDevice, c->stream));
+        }
+        if ((e = enqueue_geometry(c, g, scenes, hd, desc_src, !sync_free))) return e;
+        CK(launch_table(g, snaps, items, chunks, snap_tile, cfg, ptr<int>(c, S_REP),
+                        c->d_misc + 2, c->d_ctr, c->d_err, c->stream));
+        CK(record(c, 4));
+        return IVM_OK;
+    };
+    // ---- execute
+    if (use_graph) {
+        std::vector<unsigned long long> key = {1ull, (unsigned long long)n_scenes};
+        key_params(key, params);
+        for (int k = 0; k < n_scenes; k++) {
+            key.push_back((unsigned long long)(uintptr_t)scenes[k].facets);
+            key.push_back((unsigned long long)scenes[k].n_facets);
+            key.push_back((unsigned long long)n_snap[k]);
+            key.push_back((unsigned long long)(uintptr_t)tx[k]);
+            key.push_back((unsigned long long)(uintptr_t)rx[k]);
+            key.push_back((unsigned long long)(uintptr_t)table[k]);
+            key.push_back((unsigned long long)(uintptr_t)los[k]);
+        }
+        GraphEntry *ge = find_graph(c, key);
+        if (!ge && (r = capture_graph(c, key, sizeof(SceneDesc) * n_scenes, hd.data(), enqueue,
+                                      &ge)))
+            return r;
+        if ((r = replay(c, ge))) return r;
+    } else {
+        if ((r = enqueue(hd.data()))) return r;
+    }
+    // ---- finalize
     if ((r = read_error(c))) return r;
     for (int k = 0; k < n_scenes; k++) {
         const size_t S = (size_t)n_snap[k];
@@ -519,75 +731,97 @@ extern "C" int ivm_expand_image_tree(ivm_ctx *c, const uint32_t *matrix, const u
     } else {
         a.summary = summary;
     }
-    CK(cudaEventRecord(c->ev[0], c->stream));
-    // adjacency lists of the matrix rows
+    CK(record(c, 0));
+    // adjacency lists of the matrix rows; the column array is sized for a
+    // full matrix when that is small, so no count has to be read back
     if ((r = ensure(c, S_T_DEG, sizeof(long long) * (size_t)n))) return r;
     if ((r = ensure(c, S_T_ROW, sizeof(long long) * ((size_t)n + 1)))) return r;
     a.rowptr = ptr<long long>(c, S_T_ROW);
-    CK(tree_adjacency(a, ptr<long long>(c, S_T_DEG), c->stream));
-    long long nnz = 0;
-    CK(cudaMemcpyAsync(&nnz, a.rowptr + n, sizeof(long long), cudaMemcpyDeviceToHost, c->stream));
-    CK(cudaStreamSynchronize(c->stream));
-    if ((r = ensure(c, S_T_COL, sizeof(int) * (size_t)nnz))) return r;
+    const long long full = (long long)n * n;
+    long long nnz = full;
+    if (full > (1LL << 26)) {
+        CK(tree_adjacency(a, ptr<long long>(c, S_T_DEG), c->stream));
+        CK(cudaMemcpyAsync(&nnz, a.rowptr + n, sizeof(long long), cudaMemcpyDeviceToHost,
+                           c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+    }
+    if ((r = ensure(c, S_T_COL, sizeof(int) * (size_t)(nnz > 0 ? nnz : 1)))) return r;
     if ((r = ensure(c, S_T_WT, sizeof(unsigned long long) * 2 * (size_t)(K + 1) * n))) return r;
+    a.rowptr = ptr<long long>(c, S_T_ROW);
     a.col = ptr<int>(c, S_T_COL);
     a.wt = ptr<unsigned long long>(c, S_T_WT);
+    if (full <= (1LL << 26)) CK(tree_adjacency(a, ptr<long long>(c, S_T_DEG), c->stream));
     CK(tree_fill(a, c->stream));
-    // snapshot chunks: three vectors of n x C u64, twice, within ~768 MB
-    long long C = (768LL << 20) / (48LL * n);
-    C = C / 32 * 32;
-    if (C < 32) C = 32;
-    if (C > 8192) C = 8192;
-    if (C > S) C = (S + 31) / 32 * 32;
     if (K >= 1) {
-        const size_t xbytes = sizeof(unsigned long long) * 3 * (size_t)n * C;
+        // runs of consecutive equal Tx rows: one chain per run
+        const long long nb = (S + 255) / 256;
+        if ((r = ensure(c, S_T_FLAG, sizeof(long long) * (size_t)S))) return r;
+        if ((r = ensure(c, S_T_EXCL, sizeof(long long) * ((size_t)S + 1)))) return r;
+        if ((r = ensure(c, S_T_BS, sizeof(long long) * (size_t)nb))) return r;
+        if ((r = ensure(c, S_T_BO, sizeof(long long) * ((size_t)nb + 1)))) return r;
+        if ((r = ensure(c, S_T_RUN, sizeof(int) * (size_t)S))) return r;
+        if ((r = ensure(c, S_T_START, sizeof(long long) * (size_t)S))) return r;
+        CK(tree_tx_runs(a, ptr<long long>(c, S_T_FLAG), ptr<long long>(c, S_T_EXCL),
+                        ptr<long long>(c, S_T_BS), ptr<long long>(c, S_T_BO), ptr<int>(c, S_T_RUN),
+                        ptr<long long>(c, S_T_START), c->stream));
+        long long U = 0;
+        CK(cudaMemcpyAsync(&U, ptr<long long>(c, S_T_EXCL) + S, sizeof(long long),
+                           cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        std::vector<long long> start((size_t)U);
+        CK(cudaMemcpy(start.data(), ptr<long long>(c, S_T_START), sizeof(long long) * U,
+                      cudaMemcpyDeviceToHost));
+        // run chunks: K chains of three n x C u64 vectors within ~768 MB
+        long long C = (768LL << 20) / (24LL * K * n);
+        if (C < 1) C = 1;
+        if (C > 8192) C = 8192;
+        if (C > U) C = U;
+        const size_t xbytes = sizeof(unsigned long long) * 3 * (size_t)n * C * K;
         if ((r = ensure(c, S_T_XA, xbytes))) return r;
-        if ((r = ensure(c, S_T_XB, K >= 2 ? xbytes : 16))) return r;
-        for (long long t0 = 0; t0 < S; t0 += C) {
-            int Cc = (int)(S - t0 < C ? S - t0 : C);
-            CK(tree_chunk(a, t0, Cc, ptr<unsigned long long>(c, S_T_XA),
-                          ptr<unsigned long long>(c, S_T_XB), c->stream));
+        for (long long u0 = 0; u0 < U; u0 += C) {
+            const int Cc = (int)(U - u0 < C ? U - u0 : C);
+            const long long t0 = start[u0], t1 = u0 + Cc < U ? start[u0 + Cc] : S;
+            CK(tree_run_chunk(a, ptr<long long>(c, S_T_START), ptr<int>(c, S_T_RUN), u0, Cc, t0,
+                              t1, ptr<unsigned long long>(c, S_T_XA), c->stream));
         }
     } else {
         CK(tree_order0(a, c->stream));
     }
     int status = IVM_OK;
-    if (paths || n_paths_out) {
+    if (paths) {
         const long long items = S * (1 + (long long)K * n);
-        if (paths) {
-            if ((r = ensure(c, S_T_CNT, sizeof(long long) * (size_t)items))) return r;
-            if ((r = ensure(c, S_T_OFF, sizeof(long long) * ((size_t)items + 1)))) return r;
-            const long long nb = (items + 255) / 256;
-            if ((r = ensure(c, S_T_BS, sizeof(long long) * (size_t)nb))) return r;
-            if ((r = ensure(c, S_T_BO, sizeof(long long) * ((size_t)nb + 1)))) return r;
-            CK(tree_paths_count(a, items, ptr<long long>(c, S_T_CNT), c->stream));
-            CK(tree_scan(ptr<long long>(c, S_T_CNT), items, ptr<long long>(c, S_T_BS),
-                         ptr<long long>(c, S_T_BO), ptr<long long>(c, S_T_OFF), c->stream));
-            long long total = 0;
-            CK(cudaMemcpyAsync(&total, ptr<long long>(c, S_T_OFF) + items, sizeof(long long),
-                               cudaMemcpyDeviceToHost, c->stream));
-            CK(cudaStreamSynchronize(c->stream));
-            const bool paths_host = path_capacity > 0 && !is_device(paths);
-            int *dst = paths;
-            const long long wrote = total < path_capacity ? total : path_capacity;
-            if (paths_host) {
-                if ((r = ensure(c, S_T_PATHS, sizeof(int) * (size_t)wrote * (K + 2)))) return r;
-                dst = ptr<int>(c, S_T_PATHS);
-            }
-            if (wrote > 0)
-                CK(tree_paths_write(a, items, ptr<long long>(c, S_T_OFF), dst, path_capacity,
-                                    c->stream));
-            if (paths_host && wrote > 0)
-                CK(cudaMemcpyAsync(paths, dst, sizeof(int) * (size_t)wrote * (K + 2),
-                                   cudaMemcpyDeviceToHost, c->stream));
-            if (n_paths_out) *n_paths_out = total;
-            if (total > path_capacity) status = IVM_ERR_CAPACITY;
+        if ((r = ensure(c, S_T_CNT, sizeof(long long) * (size_t)items))) return r;
+        if ((r = ensure(c, S_T_OFF, sizeof(long long) * ((size_t)items + 1)))) return r;
+        const long long nb = (items + 255) / 256;
+        if ((r = ensure(c, S_T_BS, sizeof(long long) * (size_t)nb))) return r;
+        if ((r = ensure(c, S_T_BO, sizeof(long long) * ((size_t)nb + 1)))) return r;
+        CK(tree_paths_count(a, items, ptr<long long>(c, S_T_CNT), c->stream));
+        CK(tree_scan(ptr<long long>(c, S_T_CNT), items, ptr<long long>(c, S_T_BS),
+                     ptr<long long>(c, S_T_BO), ptr<long long>(c, S_T_OFF), c->stream));
+        long long total = 0;
+        CK(cudaMemcpyAsync(&total, ptr<long long>(c, S_T_OFF) + items, sizeof(long long),
+                           cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        const bool paths_host = path_capacity > 0 && !is_device(paths);
+        int *dst = paths;
+        const long long wrote = total < path_capacity ? total : path_capacity;
+        if (paths_host) {
+            if ((r = ensure(c, S_T_PATHS, sizeof(int) * (size_t)wrote * (K + 2)))) return r;
+            dst = ptr<int>(c, S_T_PATHS);
         }
+        if (wrote > 0)
+            CK(tree_paths_write(a, items, ptr<long long>(c, S_T_OFF), dst, path_capacity,
+                                c->stream));
+        if (paths_host && wrote > 0)
+            CK(cudaMemcpyAsync(paths, dst, sizeof(int) * (size_t)wrote * (K + 2),
+                               cudaMemcpyDeviceToHost, c->stream));
+        if (n_paths_out) *n_paths_out = total;
+        if (total > path_capacity) status = IVM_ERR_CAPACITY;
     }
     if (sum_host)
         CK(cudaMemcpyAsync(summary, a.summary, sizeof(ivm_tree_summary) * (size_t)S * (K + 1),
                            cudaMemcpyDeviceToHost, c->stream));
-    CK(cudaEventRecord(c->ev[4], c->stream));
+    CK(record(c, 4));
     CK(cudaStreamSynchronize(c->stream));
     if (n_paths_out && !paths) {
         // total path count from the summaries: sum over t and k of count

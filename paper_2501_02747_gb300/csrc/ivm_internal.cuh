@@ -119,6 +119,7 @@ struct LaunchCfg {
     int n_sm;
     int cache;            // occluder cache in front of the BVH walk
     int dedup;            // table: compute one row per run of equal source positions
+    const unsigned long long *count_dev = nullptr;  // matrix, persistent: device pair count
 };
 
 cudaError_t launch_matrix(const DevScenes &g, const int2 *pairs, unsigned long long npairs,

@@ -63,12 +63,16 @@ __device__ __forceinline__ void decide_pair(const DevScenes &g, int gi, int gj, 
 template <bool PERSIST, bool CACHE, class LeafFn>
 __global__ void __launch_bounds__(kTravThreads, IVM_MIN_BLOCKS)
 k_matrix(DevScenes g, const int2 *pairs, unsigned long long npairs, int tile,
-                         unsigned long long *work, unsigned long long *ctr, int *err)
+         const unsigned long long *count_dev, unsigned long long *work, unsigned long long *ctr,
+         int *err)
 {
     WalkCounters wc;
     LeafFn leaf;
     OccluderCache cache;
     const int lane = threadIdx.x & 31;
+    // persistent launches may take the pair count from the screen's device
+    // counter (written by an earlier kernel on the same stream)
+    if (PERSIST && count_dev) npairs = min(npairs, *count_dev);
     if (!PERSIST) {
         unsigned long long w = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
         if (w < npairs) {
@@ -103,10 +107,11 @@ static void launch_one(const DevScenes &g, const int2 *pairs, unsigned long long
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, 0);
         int blocks = cfg.n_sm * (per_sm > 0 ? per_sm : 1);
         cudaMemsetAsync(work, 0, sizeof(unsigned long long), st);
-        kern<<<blocks, threads, 0, st>>>(g, pairs, npairs, cfg.tile, work, ctr, err);
+        kern<<<blocks, threads, 0, st>>>(g, pairs, npairs, cfg.tile, cfg.count_dev, work, ctr,
+                                         err);
     } else {
         unsigned long long blocks = (npairs + cfg.warps_per_block - 1) / cfg.warps_per_block;
-        kern<<<(unsigned)blocks, threads, 0, st>>>(g, pairs, npairs, 1, work, ctr, err);
+        kern<<<(unsigned)blocks, threads, 0, st>>>(g, pairs, npairs, 1, nullptr, work, ctr, err);
     }
 }
 

@@ -115,49 +115,86 @@ __device__ __forceinline__ bool row_bit(const uint32_t *table, int W, long long 
     return (table[((size_t)t * 2 + side) * W + (f >> 5)] >> (f & 31)) & 1u;
 }
 
-// x[c][f][tl] for the chunk's snapshots
-__global__ void k_init(TreeArgs a, long long t0, int C, unsigned long long *x)
+// The Tx-side chain x_1 .. x_K depends on the snapshot only through its Tx
+// row, so it is computed once per run of consecutive equal Tx rows (a
+// static Tx is one run); each snapshot then only takes the dot products
+// with its own Rx row.
+
+// flag[t] = 1 when Tx row t differs from Tx row t-1 (warp per snapshot)
+__global__ void k_tx_run_flags(TreeArgs a, long long *flag)
 {
-    int tl = blockIdx.x * blockDim.x + threadIdx.x;
+    const long long t = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (t >= a.S) return;
+    bool diff = t == 0;
+    if (t > 0) {
+        const uint32_t *r0 = a.table + (size_t)t * 2 * a.W;
+        const uint32_t *r1 = a.table + (size_t)(t - 1) * 2 * a.W;
+        for (int w = lane; w < a.W && !diff; w += 32) diff = r0[w] != r1[w];
+    }
+    diff = __any_sync(0xffffffffu, diff);
+    if (lane == 0) flag[t] = diff ? 1 : 0;
+}
+
+// run_of[t] from the exclusive scan of the flags; start[u] = first t of run u
+__global__ void k_tx_runs(TreeArgs a, const long long *flag, const long long *excl,
+                          int *run_of, long long *start)
+{
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= a.S) return;
+    const long long u = excl[t] + flag[t] - 1;
+    run_of[t] = (int)u;
+    if (flag[t]) start[u] = t;
+}
+
+// x_1[c][f][ul] for the runs u0 .. u0 + C - 1
+__global__ void k_init_runs(TreeArgs a, const long long *start, long long u0, int C,
+                            unsigned long long *x)
+{
+    int ul = blockIdx.x * blockDim.x + threadIdx.x;
     int f = blockIdx.y;
-    if (tl >= C || t0 + tl >= a.S) return;
-    bool v = row_bit(a.table, a.W, t0 + tl, 0, f);
+    if (ul >= C) return;
+    bool v = row_bit(a.table, a.W, start[u0 + ul], 0, f);
     size_t plane = (size_t)a.n * C;
-    size_t o = (size_t)f * C + tl;
+    size_t o = (size_t)f * C + ul;
     x[o] = v ? 1ull : 0ull;
     x[plane + o] = v ? a.wt[(size_t)1 * a.n + f] : 0ull;
     x[2 * plane + o] = v ? a.wt[(size_t)(a.K + 1) * a.n + (size_t)1 * a.n + f] : 0ull;
 }
 
-// summary[t][k] = sum_f x[c][f][t] vis_Rx[t][f]; order 0 from los when k == 1
-__global__ void k_dot(TreeArgs a, long long t0, int C, int k, const unsigned long long *x)
+// For snapshots [t0, t1) (all in runs u0 .. u0 + C - 1): summary[t][k] =
+// sum_g x_k[c][g][run(t) - u0] vis_Rx[t][g] for k = 1..K, and order 0.
+// xs holds x_1 .. x_K, 3 n C words each.
+__global__ void k_dot_runs(TreeArgs a, const int *run_of, long long t0, long long t1,
+                           long long u0, int C, const unsigned long long *xs)
 {
-    int tl = blockIdx.x * blockDim.x + threadIdx.x;
-    long long t = t0 + tl;
-    if (tl >= C || t >= a.S) return;
-    size_t plane = (size_t)a.n * C;
-    unsigned long long s0 = 0, s1 = 0, s2 = 0;
+    const long long t = t0 + (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= t1) return;
+    const int ul = (int)(run_of[t] - u0);
+    const size_t plane = (size_t)a.n * C;
     const uint32_t *rx = a.table + ((size_t)t * 2 + 1) * a.W;
-    for (int w = 0; w < a.W; w++) {
-        uint32_t word = rx[w];
-        while (word) {
-            int b = __ffs(word) - 1;
-            word &= word - 1;
-            size_t o = (size_t)(32 * w + b) * C + tl;
-            s0 += x[o];
-            s1 += x[plane + o];
-            s2 += x[2 * plane + o];
-        }
-    }
     ivm_tree_summary *out = a.summary + (size_t)t * (a.K + 1);
-    out[k].count = s0;
-    out[k].fp0 = s1;
-    out[k].fp1 = s2;
-    if (k == 1) {
-        unsigned long long l = a.los[t] ? 1ull : 0ull;
-        out[0].count = l;
-        out[0].fp0 = l;
-        out[0].fp1 = l;
+    const unsigned long long l = a.los[t] ? 1ull : 0ull;
+    out[0].count = l;
+    out[0].fp0 = l;
+    out[0].fp1 = l;
+    for (int k = 1; k <= a.K; k++) {
+        const unsigned long long *x = xs + (size_t)(k - 1) * 3 * plane;
+        unsigned long long s0 = 0, s1 = 0, s2 = 0;
+        for (int w = 0; w < a.W; w++) {
+            uint32_t word = rx[w];
+            while (word) {
+                int b = __ffs(word) - 1;
+                word &= word - 1;
+                size_t o = (size_t)(32 * w + b) * C + ul;
+                s0 += x[o];
+                s1 += x[plane + o];
+                s2 += x[2 * plane + o];
+            }
+        }
+        out[k].count = s0;
+        out[k].fp0 = s1;
+        out[k].fp1 = s2;
     }
 }
 
@@ -328,20 +365,32 @@ cudaError_t tree_fill(TreeArgs &a, cudaStream_t st)
     return cudaGetLastError();
 }
 
-cudaError_t tree_chunk(TreeArgs &a, long long t0, int C, unsigned long long *xa,
-                       unsigned long long *xb, cudaStream_t st)
+cudaError_t tree_tx_runs(TreeArgs &a, long long *flag, long long *excl, long long *bsum,
+                         long long *boff, int *run_of, long long *start, cudaStream_t st)
 {
+    k_tx_run_flags<<<(unsigned)((a.S * 32 + 255) / 256), 256, 0, st>>>(a, flag);
+    cudaError_t e = tree_scan(flag, a.S, bsum, boff, excl, st);
+    if (e != cudaSuccess) return e;
+    k_tx_runs<<<(unsigned)((a.S + 255) / 256), 256, 0, st>>>(a, flag, excl, run_of, start);
+    note_launches(2);
+    return cudaGetLastError();
+}
+
+// Runs [u0, u0 + C) covering snapshots [t0, t1): chains x_1..x_K into xs
+// (K blocks of 3 n C words), then the dots of every snapshot of those runs.
+cudaError_t tree_run_chunk(TreeArgs &a, const long long *start, const int *run_of, long long u0,
+                           int C, long long t0, long long t1, unsigned long long *xs,
+                           cudaStream_t st)
+{
+    const size_t block = (size_t)3 * a.n * C;
     dim3 gi((C + 127) / 128, a.n);
-    k_init<<<gi, 128, 0, st>>>(a, t0, C, xa);
-    k_dot<<<(C + 127) / 128, 128, 0, st>>>(a, t0, C, 1, xa);
-    unsigned long long *xo = xa, *xn = xb;
+    k_init_runs<<<gi, 128, 0, st>>>(a, start, u0, C, xs);
     const long long warps = (long long)a.n * ((C + 31) / 32);
-    for (int k = 2; k <= a.K; k++) {
-        k_hop<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, st>>>(a, C, k, xo, xn);
-        k_dot<<<(C + 127) / 128, 128, 0, st>>>(a, t0, C, k, xn);
-        unsigned long long *tmp = xo; xo = xn; xn = tmp;
-    }
-    note_launches(2 + 2 * (a.K - 1));
+    for (int k = 2; k <= a.K; k++)
+        k_hop<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, st>>>(
+            a, C, k, xs + (k - 2) * block, xs + (k - 1) * block);
+    k_dot_runs<<<(unsigned)((t1 - t0 + 127) / 128), 128, 0, st>>>(a, run_of, t0, t1, u0, C, xs);
+    note_launches(2 + (a.K - 1));
     return cudaGetLastError();
 }
 

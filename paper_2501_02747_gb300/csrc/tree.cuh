@@ -19,8 +19,11 @@ struct TreeArgs {
 
 cudaError_t tree_adjacency(TreeArgs &a, long long *deg, cudaStream_t st);
 cudaError_t tree_fill(TreeArgs &a, cudaStream_t st);
-cudaError_t tree_chunk(TreeArgs &a, long long t0, int C, unsigned long long *xa,
-                       unsigned long long *xb, cudaStream_t st);
+cudaError_t tree_tx_runs(TreeArgs &a, long long *flag, long long *excl, long long *bsum,
+                         long long *boff, int *run_of, long long *start, cudaStream_t st);
+cudaError_t tree_run_chunk(TreeArgs &a, const long long *start, const int *run_of, long long u0,
+                           int C, long long t0, long long t1, unsigned long long *xs,
+                           cudaStream_t st);
 cudaError_t tree_order0(TreeArgs &a, cudaStream_t st);
 cudaError_t tree_paths_count(TreeArgs &a, long long items, long long *cnt, cudaStream_t st);
 cudaError_t tree_scan(const long long *in, long long n, long long *sums, long long *sums_off,

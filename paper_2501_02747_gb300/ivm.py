@@ -258,9 +258,10 @@ def ivm_build_table(ctx, facets, s, tx, rx, mode=IVM_MODE_EXACT, flags=0, tile=0
 
 
 def ivm_expand_image_tree(ctx, matrix, table, los, n_facets, max_order, paths_capacity=None,
-                          summary=None, paths=None):
-    """Summaries uint64 [S][K+1][3] (torch, on device unless `summary` is given);
-    with paths_capacity, also the path records int32 [n][K+2] and the total."""
+                          summary=None, paths=None, count_paths=False):
+    """Summaries uint64 [S][K+1][3] (torch, on device unless `summary` is given)
+    and, with count_paths, the total number of paths (else None); with
+    paths_capacity, also the path records int32 [n][K+2] and the total."""
     import torch
     S = int(table.shape[0])
     K = int(max_order)
@@ -273,13 +274,14 @@ def ivm_expand_image_tree(ctx, matrix, table, los, n_facets, max_order, paths_ca
         if paths is None:
             paths = torch.empty((max(cap, 1), K + 2), dtype=torch.int32,
                                 device=f"cuda:{ctx.device}")
+    want_total = count_paths or paths_capacity is not None
     code = lib().ivm_expand_image_tree(ctx.handle, _addr(matrix), _addr(table), _addr(los),
                                        int(n_facets), S, K, _addr(summary),
                                        _addr(paths) if paths_capacity is not None else None,
-                                       cap, ctypes.byref(total))
+                                       cap, ctypes.byref(total) if want_total else None)
     if code == IVM_ERR_CAPACITY:
         return summary, paths, int(total.value), code
     _check(code, "ivm_expand_image_tree")
     if paths_capacity is not None:
         return summary, paths[:min(cap, total.value)], int(total.value), code
-    return summary, int(total.value)
+    return summary, (int(total.value) if want_total else None)

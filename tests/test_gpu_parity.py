@@ -106,6 +106,39 @@ def test_dedup_with_runs_of_equal_positions(ctx):
         assert st.dedup_rows == 2 * 20 - runs
 
 
+def test_graph_replay_rereads_inputs(ctx):
+    """IVM_FLAG_GRAPH: the first call captures, later calls with the same
+    buffers replay; the buffers' contents change between calls (two scenes
+    of equal size in the same device buffers) and every result must match
+    the plain form on that content."""
+    import torch
+    GRAPH = FAST | ivm.IVM_FLAG_GRAPH
+    a = sg.random_small_city(441, n_buildings=6, side=9000, n_snap=40, s=2)
+    b = sg.random_small_city(442, n_buildings=6, side=9000, n_snap=40, s=2)
+    assert a.n_facets == b.n_facets
+    n, S = a.n_facets, a.n_snap
+    F = torch.empty((n, 10), dtype=torch.int32, device="cuda")
+    tx = torch.empty((S, 3), dtype=torch.int32, device="cuda")
+    rx = torch.empty((S, 3), dtype=torch.int32, device="cuda")
+    M = torch.empty((n, ivm.words(n)), dtype=torch.int32, device="cuda")
+    T = torch.empty((S, 2, ivm.words(n)), dtype=torch.int32, device="cuda")
+    L = torch.empty((S,), dtype=torch.uint8, device="cuda")
+    l0 = ivm.kernel_launches()
+    for rep in range(3):
+        for sc in (a, b):
+            F.copy_(torch.from_numpy(sc.facets))
+            tx.copy_(torch.from_numpy(sc.tx))
+            rx.copy_(torch.from_numpy(sc.rx))
+            ivm.ivm_build_matrix(ctx, F, 2, mode=ivm.IVM_MODE_FILTERED, flags=GRAPH, out=M)
+            ivm.ivm_build_table(ctx, F, 2, tx, rx, mode=ivm.IVM_MODE_FILTERED, flags=GRAPH,
+                                out=(T, L))
+            Mp, _ = gpu_matrix(ctx, sc.facets, 2)
+            Tp, Lp, _ = gpu_table(ctx, sc.facets, 2, sc.tx, sc.rx)
+            assert (to_np(M) == Mp).all() and (to_np(T) == Tp).all()
+            assert (L.cpu().numpy() == Lp).all()
+    assert ivm.kernel_launches() > l0   # replays are counted as launches
+
+
 def test_many_samples_table_path(ctx):
     """s = 6 and 8: s*s > 32 samples per facet take several packets."""
     sc = sg.random_small_city(411, n_buildings=3, side=6000, n_snap=10, s=6)

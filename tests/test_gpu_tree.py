@@ -25,7 +25,7 @@ def gpu_all(ctx, sc, K, mode=ivm.IVM_MODE_EXACT):
     s = sc.samples_per_side
     M, _ = ivm.ivm_build_matrix(ctx, sc.facets, s, mode=mode)
     (T, L), _ = ivm.ivm_build_table(ctx, sc.facets, s, sc.tx, sc.rx, mode=mode)
-    summ, total = ivm.ivm_expand_image_tree(ctx, M, T, L, sc.n_facets, K)
+    summ, total = ivm.ivm_expand_image_tree(ctx, M, T, L, sc.n_facets, K, count_paths=True)
     return M, T, L, to_np(summ), total
 
 
@@ -63,6 +63,22 @@ def test_random_small_summaries(ctx, seed, K):
     Mo = oracle.matrix(sc.facets, 2)
     tab, los = oracle.table(sc.facets, 2, sc.tx, sc.rx)
     assert (summ == oracle.tree(Mo, tab, los, sc.n_facets, K)).all()
+
+
+def test_tx_runs_of_uneven_length(ctx):
+    """The Tx-side chain is shared by a run of equal Tx rows: runs of length
+    1, 2, 5, ... and a moving Rx must give the oracle's summaries."""
+    sc = sg.random_small_city(521, n_buildings=5, side=9000, n_snap=12, s=2)
+    idx = np.repeat(np.arange(12), [1, 2, 5, 1, 3, 1, 1, 4, 2, 1, 6, 1])
+    tx = sc.tx[idx]
+    rx = sg.random_small_city(522, n_buildings=5, side=9000, n_snap=len(idx), s=2).rx
+    n, K = sc.n_facets, 3
+    M, _ = ivm.ivm_build_matrix(ctx, sc.facets, 2)
+    (T, L), _ = ivm.ivm_build_table(ctx, sc.facets, 2, tx, rx)
+    summ, _ = ivm.ivm_expand_image_tree(ctx, M, T, L, n, K)
+    Mo = oracle.matrix(sc.facets, 2)
+    tab, los = oracle.table(sc.facets, 2, tx, rx)
+    assert (to_np(summ) == oracle.tree(Mo, tab, los, n, K)).all()
 
 
 def test_oracle_inputs_in_host_memory(ctx):

@@ -45,7 +45,7 @@ __device__ __forceinline__ void decide_pair(const DevScenes &g, int gi, int gj, 
         unsigned alive = __ballot_sync(kFull, face);
         if (!alive) continue;
         wc.segments += face;
-        const Seg sg = make_seg(px, py, pz, qx, qy, qz);
+        Seg sg = make_seg(px, py, pz, qx, qy, qz);
         int myblk = -1;
         alive = occlude<CACHE>(sg, alive, g.nodes, g.leaf, D.root, dirx, diry, dirz, budget, err,
                                wc, leaf, cache, myblk);

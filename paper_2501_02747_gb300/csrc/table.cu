@@ -29,6 +29,11 @@
 
 namespace ivm {
 
+// Table packet strategy: probe the previously seen sample first; test the
+// warp's recently used occluders before a walk.
+constexpr bool kTableProbe = true;
+constexpr bool kTableLru = true;
+
 __device__ __forceinline__ int scene_of_snap(const SceneDesc *desc, int n_scenes, long long T)
 {
     int lo = 0, hi = n_scenes - 1;
@@ -65,20 +70,35 @@ __device__ __forceinline__ bool in_range(long long x, long long y, long long z)
            (z > -kCoordLimit) & (z < kCoordLimit);
 }
 
-// Packet of segments from (x, y, z) to samples of facets of word c; returns
-// the lanes left unblocked.  Tests the lane's temporal blocker `tb` first.
+// Packet of segments from (x, y, z) to samples of facets of word c.  Lane
+// takes sample b of the packet's group gi (lanes gi*s2 .. gi*s2 + s2 - 1).
+// Returns a lane mask in which a group has a set bit iff some segment of
+// that group is unblocked (its facet is visible); bits of unblocked lanes
+// are exact, a group settled by its probe keeps only the probe's bit.
+// With the caches on, each lane first tests `tb`, the facet that hid its
+// facet at the previous snapshot; then each group whose facet was visible
+// at the previous snapshot through sample pf walks that one segment first,
+// and if it is free the rest of the group is skipped.
 template <bool CACHE, class LeafFn>
 __device__ __forceinline__ unsigned table_packet(const DevScenes &g, const SceneDesc &D, bool mine,
                                                  int sidx, int lead, int x, int y, int z,
-                                                 int tb, int *err, WalkCounters &wc,
-                                                 LeafFn leaf, OccluderCache &cache, int &myblk)
+                                                 int tb, int pf, int gi, int b, int s2, int *err,
+                                                 WalkCounters &wc, LeafFn leaf,
+                                                 OccluderCache &cache, int &myblk)
 {
+    const int lane = threadIdx.x & 31;
     int qx = 0, qy = 0, qz = 0;
     if (mine) { qx = __ldg(g.sx + sidx); qy = __ldg(g.sy + sidx); qz = __ldg(g.sz + sidx); }
     unsigned alive = __ballot_sync(kFull, mine);
     wc.segments += mine;
-    const Seg sg = make_seg(x, y, z, qx, qy, qz);
+    Seg sg = make_seg(x, y, z, qx, qy, qz);
     myblk = -1;
+    const Leaf Lf = load_leaf(g.leaf, lead);
+    const float dirx = (float)(2 * Lf.ox + Lf.ux + Lf.vx - 2 * x);
+    const float diry = (float)(2 * Lf.oy + Lf.uy + Lf.vy - 2 * y);
+    const float dirz = (float)(2 * Lf.oz + Lf.uz + Lf.vz - 2 * z);
+    const int budget = 4 * D.n + 16;
+    unsigned shown = 0;   // probe lanes found free
     if (CACHE) {
         bool hit = false;
         if (mine && tb >= 0) {
@@ -88,13 +108,21 @@ __device__ __forceinline__ unsigned table_packet(const DevScenes &g, const Scene
         if (hit) { myblk = tb; wc.cache_hits++; }
         alive &= ~__ballot_sync(kFull, hit);
         if (!alive) return 0;
+        const bool probe = kTableProbe && mine && pf >= 0 && b == pf && ((alive >> lane) & 1u);
+        const unsigned pm = __ballot_sync(kFull, probe);
+        if (pm) {
+            shown = pm & occlude<CACHE, LeafFn, false>(sg, pm, g.nodes, g.leaf, D.root, dirx,
+                                                       diry, dirz, budget,
+                                        err, wc, leaf, cache, myblk);
+            // groups whose probe is free are visible: their other lanes need no walk
+            const bool done = mine && pf >= 0 && ((shown >> (gi * s2 + pf)) & 1u);
+            alive &= ~(__ballot_sync(kFull, done) | pm);
+            if (!alive) return shown;
+        }
     }
-    const Leaf Lf = load_leaf(g.leaf, lead);
-    const float dirx = (float)(2 * Lf.ox + Lf.ux + Lf.vx - 2 * x);
-    const float diry = (float)(2 * Lf.oy + Lf.uy + Lf.vy - 2 * y);
-    const float dirz = (float)(2 * Lf.oz + Lf.uz + Lf.vz - 2 * z);
-    return occlude<CACHE>(sg, alive, g.nodes, g.leaf, D.root, dirx, diry, dirz, 4 * D.n + 16, err,
-                          wc, leaf, cache, myblk);
+    return shown | occlude<CACHE, LeafFn, CACHE && kTableLru>(sg, alive, g.nodes, g.leaf, D.root,
+                                                             dirx, diry, dirz, budget,
+                                  err, wc, leaf, cache, myblk);
 }
 
 template <bool CACHE, class LeafFn>
@@ -124,6 +152,7 @@ __device__ __forceinline__ void table_tile(const DevScenes &g, long long item, i
     const int s2 = D.s * D.s;
     const long long k = 2LL * D.s;
     int prev_blk = -1;   // lane l: facet that last blocked facet 32c + l
+    int prev_free = -1;  // lane l: sample of facet 32c + l seen at the previous snapshot
     for (long long t = t0; t < t1; t++) {
         if (rep && rep[2 * (D.snap0 + t) + side] != t) continue;   // copied later
         uint32_t *row = D.table + ((size_t)t * 2 + side) * D.W;
@@ -151,19 +180,27 @@ __device__ __forceinline__ void table_tile(const DevScenes &g, long long item, i
                 const int jbit = mine ? __ffs(m) - 1 : 0;
                 const int sidx = D.sample0 + (32 * c + jbit) * s2 + b;
                 const int tb = __shfl_sync(kFull, prev_blk, jbit);
+                const int pf = __shfl_sync(kFull, prev_free, jbit);
                 const int lead = D.facet0 + 32 * c + __shfl_sync(kFull, jbit, 0);
                 int myblk;
                 const unsigned alive = table_packet<CACHE>(g, D, mine, sidx, lead, x, y, z, tb,
-                                                           err, wc, leaf, cache, myblk);
+                                                           pf, gi, b, s2, err, wc, leaf, cache,
+                                                           myblk);
                 const unsigned smask = (s2 == 32) ? kFull : ((1u << s2) - 1u);
-                const bool gvis = mine && ((alive >> (gi * s2)) & smask) != 0u;
+                const unsigned gbits = (alive >> (gi * s2)) & smask;
+                const bool gvis = mine && gbits != 0u;
                 word |= __reduce_or_sync(kFull, (gvis && b == 0) ? (1u << jbit) : 0u);
                 if (CACHE) {
-                    for (int q = 0; q < cnt; q++) {   // remember each hidden facet's blocker
+                    // per facet: the blocker that hid it, or the sample it was seen through
+                    const int fs = gvis ? __ffs(gbits) - 1 : -1;
+                    for (int q = 0; q < cnt; q++) {
                         const int jb = __shfl_sync(kFull, jbit, q * s2);
                         const int nb = __shfl_sync(kFull, myblk, q * s2);
-                        const bool vis = __shfl_sync(kFull, gvis, q * s2);
-                        if (lane == jb && !vis && nb >= 0) prev_blk = nb;
+                        const int f1 = __shfl_sync(kFull, fs, q * s2);
+                        if (lane == jb) {
+                            prev_free = f1;
+                            if (f1 < 0 && nb >= 0) prev_blk = nb;
+                        }
                     }
                 }
                 for (int q = 0; q < cnt; q++) fm &= fm - 1;
@@ -179,7 +216,7 @@ __device__ __forceinline__ void table_tile(const DevScenes &g, long long item, i
                     int myblk;
                     const unsigned alive = table_packet<CACHE>(
                         g, D, b < s2, D.sample0 + jlocal * s2 + b, D.facet0 + jlocal, x, y, z,
-                        tb, err, wc, leaf, cache, myblk);
+                        tb, -1, 0, b, 32, err, wc, leaf, cache, myblk);
                     if (alive) {
                         vis = true;
                         break;
@@ -216,7 +253,7 @@ __device__ __forceinline__ void los_item(const DevScenes &g, long long chunk, in
     const bool test = valid && ok && !same;
     unsigned alive = __ballot_sync(kFull, test);
     wc.segments += test;
-    const Seg sg = make_seg((int)a0, (int)a1, (int)a2, (int)b0, (int)b1, (int)b2);
+    Seg sg = make_seg((int)a0, (int)a1, (int)a2, (int)b0, (int)b1, (int)b2);
     const int lead = __ffs(alive | 1u) - 1;
     const float dirx = (float)__shfl_sync(kFull, sg.dx, lead);
     const float diry = (float)__shfl_sync(kFull, sg.dy, lead);

@@ -30,16 +30,23 @@ struct Seg {
     float ix, iy, iz;     // round-to-nearest reciprocal of d; 2^100 where d == 0
 };
 
+// The reciprocals are only needed by box tests; finish_seg computes them
+// right before a BVH walk, so segments settled by cached occluders skip it.
 __device__ __forceinline__ Seg make_seg(int px, int py, int pz, int qx, int qy, int qz)
 {
     Seg s;
     s.px = px; s.py = py; s.pz = pz;
     s.dx = qx - px; s.dy = qy - py; s.dz = qz - pz;
     s.fpx = (float)px; s.fpy = (float)py; s.fpz = (float)pz;
+    s.ix = s.iy = s.iz = 0.f;
+    return s;
+}
+
+__device__ __forceinline__ void finish_seg(Seg &s)
+{
     s.ix = s.dx ? __frcp_rn((float)s.dx) : 0x1p100f;
     s.iy = s.dy ? __frcp_rn((float)s.dy) : 0x1p100f;
     s.iz = s.dz ? __frcp_rn((float)s.dz) : 0x1p100f;
-    return s;
 }
 
 // Conservative segment-box test: true whenever the open segment touches the
@@ -317,14 +324,14 @@ struct OccluderCache {
 // Lanes of the packet left unblocked: cached occluders first (when `cache`),
 // then the BVH walk.  Same contract as walk_packet; `myblk` receives, in each
 // lane that gets blocked, the facet that blocked it.
-template <bool CACHE, class LeafFn>
-__device__ __forceinline__ unsigned occlude(const Seg &s, unsigned alive, const Node *nodes,
+template <bool CACHE, class LeafFn, bool LRU = CACHE>
+__device__ __forceinline__ unsigned occlude(Seg &s, unsigned alive, const Node *nodes,
                                             const Leaf *leaves, int root, float dirx, float diry,
                                             float dirz, int budget, int *err, WalkCounters &wc,
                                             LeafFn leaf_hit, OccluderCache &cache, int &myblk)
 {
     const int lane = threadIdx.x & 31;
-    if (CACHE) {
+    if (CACHE && LRU) {
         int promote = -1;
 #pragma unroll
         for (int k = 0; k < kCacheSize; k++) {
@@ -344,6 +351,7 @@ __device__ __forceinline__ unsigned occlude(const Seg &s, unsigned alive, const 
         if (!alive) return 0;
     }
     int blocker;
+    if (s.ix == 0.f) finish_seg(s);   // reciprocals only when walking
     alive = walk_packet(s, alive, nodes, leaves, root, dirx, diry, dirz, budget, err, wc,
                         leaf_hit, blocker, myblk);
     if (CACHE) cache.put(blocker);

@@ -236,15 +236,23 @@ def run_ours(args, ws, rank, local):
                      | ivm.IVM_FLAG_DEDUP_SOURCES | ivm.IVM_FLAG_GRAPH),
     }
 
+    # launch shape of the fast form from the library's autotuner (untimed)
+    tuned = ivm.ivm_autotune(ctx, facets_d, s, tx_d, rx_d, mode=forms["fast"]["mode"],
+                             flags=forms["fast"]["flags"])
+    shape = {"plain": ({}, {}),
+             "fast": ({"tile": tuned["tile"], "warps_per_block": tuned["warps_per_block"]},
+                      {"tile": tuned["table_tile"], "warps_per_block": tuned["warps_per_block"]})}
+
     def step(form, fac, tx, rx, M, T, L, summ, marks=None):
         """The three calls; `marks` (4 CUDA events) bracket them on the stream."""
         kw = forms[form]
+        kw_m, kw_t = shape[form]
         if marks:
             marks[0].record(stream)
-        _, stm = ivm.ivm_build_matrix(ctx, fac, s, out=M, **kw)
+        _, stm = ivm.ivm_build_matrix(ctx, fac, s, out=M, **kw, **kw_m)
         if marks:
             marks[1].record(stream)
-        _, stt = ivm.ivm_build_table(ctx, fac, s, tx, rx, out=(T, L), **kw)
+        _, stt = ivm.ivm_build_table(ctx, fac, s, tx, rx, out=(T, L), **kw, **kw_t)
         if marks:
             marks[2].record(stream)
         ivm.ivm_expand_image_tree(ctx, M, T, L, N, K, summary=summ)
@@ -329,7 +337,7 @@ def run_ours(args, ws, rank, local):
                    "source positions, CUDA-graph replay of each call",
                    "l2": "flushed between steps (512 MB write)",
                    "facets": N, "snapshots": S, "samples_per_side": s, "max_order": K,
-                   "pair_tests_per_step": units},
+                   "pair_tests_per_step": units, "autotuned_shape": tuned},
         "snapshot_tables_per_s": ws * S / (ms_fast / 1e3),
         "plain": {"ms_per_step": ms_plain, "value": ws * units / (ms_plain / 1e3),
                   "form": "exact int64/int128 facet tests, one warp per work item"},

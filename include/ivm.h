@@ -93,10 +93,10 @@ typedef struct ivm_params {
     int32_t samples_per_side; /* s, 1..8 */
     int32_t max_order;        /* K for ivm_expand_image_tree, 0..8 */
     int32_t mode;             /* IVM_MODE_* */
-    int32_t tile;             /* matrix: pairs per queue pop; table: consecutive
-                                 snapshots per work item (0 = default) */
+    int32_t tile;             /* matrix: candidate pairs per queue pop (0 = default) */
     int32_t warps_per_block;  /* 1..4 (0 = default 4) */
     int32_t flags;            /* IVM_FLAG_* */
+    int32_t table_tile;       /* table: consecutive snapshots per work item (0 = 16) */
 } ivm_params;
 
 typedef struct ivm_stats {
@@ -170,6 +170,19 @@ int ivm_expand_image_tree(ivm_ctx *ctx, const uint32_t *matrix, const uint32_t *
                           const uint8_t *los, int32_t n_facets, int64_t n_snap,
                           int32_t max_order, ivm_tree_summary *summary, int32_t *paths,
                           int64_t path_capacity, int64_t *n_paths_out);
+
+/* Autotuner for the batched / persistent form (not in the paper: a launch
+ * schedule choice).  Times candidate launch shapes on a sample of the given
+ * workload -- the first 8 scenes at most and the first 16,384 snapshots of
+ * each -- with params' samples_per_side, mode and flags (graph replay is
+ * switched off while timing), and writes the fastest warps_per_block, tile
+ * and table_tile into *params.  Inputs as for ivm_build_table (host or
+ * device; tx, rx, n_snap may be NULL to tune the matrix only).  The outputs
+ * of the trial runs go to the context's scratch.  Errors: as
+ * ivm_build_table. */
+int ivm_autotune(ivm_ctx *ctx, const ivm_scene *scenes, int32_t n_scenes,
+                 const int32_t *const *tx, const int32_t *const *rx, const int64_t *n_snap,
+                 ivm_params *params);
 
 /* Message for an error code (static string). */
 const char *ivm_strerror(int code);

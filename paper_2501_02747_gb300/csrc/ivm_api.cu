@@ -30,6 +30,7 @@ enum Slot {
     S_ORDER, S_NODES, S_PARENT, S_VISITS, S_PAIRS, S_OUT, S_TX, S_RX, S_LOS, S_REP,
     S_T_MAT, S_T_TAB, S_T_LOS, S_T_SUM, S_T_DEG, S_T_ROW, S_T_COL, S_T_WT, S_T_XA, S_T_XB,
     S_T_CNT, S_T_OFF, S_T_BS, S_T_BO, S_T_PATHS, S_T_FLAG, S_T_EXCL, S_T_RUN, S_T_START,
+    S_TUNE_M, S_TUNE_T, S_TUNE_L,
     S_COUNT
 };
 
@@ -135,6 +136,7 @@ int check_params(const ivm_params *p)
     if (p->samples_per_side < 1 || p->samples_per_side > kMaxSamplesPerSide) return IVM_ERR_ARG;
     if (p->mode < IVM_MODE_EXACT || p->mode > IVM_MODE_LEARNED) return IVM_ERR_ARG;
     if (p->tile < 0 || p->warps_per_block < 0 || p->warps_per_block > 4) return IVM_ERR_ARG;
+    if (p->table_tile < 0) return IVM_ERR_ARG;
     return IVM_OK;
 }
 
@@ -392,6 +394,7 @@ void key_params(std::vector<unsigned long long> &k, const ivm_params *p)
     k.push_back((unsigned long long)p->tile);
     k.push_back((unsigned long long)p->warps_per_block);
     k.push_back((unsigned long long)p->flags);
+    k.push_back((unsigned long long)p->table_tile);
 }
 
 }  // namespace
@@ -565,7 +568,7 @@ extern "C" int ivm_build_table(ivm_ctx *c, const ivm_scene *scenes, int32_t n_sc
     // ---- plan
     if ((r = plan_geometry(c, scenes, n_scenes, params->samples_per_side, g, hd))) return r;
     long long snaps = 0, chunks = 0, items = 0;
-    const int snap_tile = params->tile > 0 ? params->tile : 16;
+    const int snap_tile = params->table_tile > 0 ? params->table_tile : 16;
     size_t host_tab = 0, host_los = 0, pos_tx = 0, pos_rx = 0;
     std::vector<char> tab_host(n_scenes), los_host(n_scenes), tx_host(n_scenes),
         rx_host(n_scenes);
@@ -838,4 +841,100 @@ extern "C" int ivm_expand_image_tree(ivm_ctx *c, const uint32_t *matrix, const u
         *n_paths_out = tot;
     }
     return status;
+}
+
+// ============================================================================ autotuner
+
+extern "C" int ivm_autotune(ivm_ctx *c, const ivm_scene *scenes, int32_t n_scenes,
+                            const int32_t *const *tx, const int32_t *const *rx,
+                            const int64_t *n_snap, ivm_params *params)
+{
+    if (!c || !scenes || n_scenes < 1 || !params) return IVM_ERR_ARG;
+    int r = check_params(params);
+    if (r) return r;
+    DeviceGuard dg(c->device);
+    const int ns = n_scenes < 8 ? n_scenes : 8;
+    const bool with_table = tx && rx && n_snap;
+    // trial outputs in the context's scratch
+    std::vector<int64_t> snaps(ns, 0);
+    size_t mwords = 0, twords = 0, lbytes = 0;
+    for (int k = 0; k < ns; k++) {
+        if (!scenes[k].facets || scenes[k].n_facets < 1) return IVM_ERR_ARG;
+        const size_t W = (size_t)words(scenes[k].n_facets);
+        mwords += (size_t)scenes[k].n_facets * W;
+        if (with_table) {
+            if (n_snap[k] < 0) return IVM_ERR_ARG;
+            // enough snapshots that the sample has the full run's parallelism
+            snaps[k] = n_snap[k] < 16384 ? n_snap[k] : 16384;
+            twords += (size_t)snaps[k] * 2 * W;
+            lbytes += (size_t)snaps[k];
+        }
+    }
+    if ((r = ensure(c, S_TUNE_M, sizeof(uint32_t) * mwords))) return r;
+    if ((r = ensure(c, S_TUNE_T, sizeof(uint32_t) * twords))) return r;
+    if ((r = ensure(c, S_TUNE_L, lbytes))) return r;
+    std::vector<uint32_t *> mout(ns), tout(ns);
+    std::vector<uint8_t *> lout(ns);
+    size_t om = 0, ot = 0, ol = 0;
+    for (int k = 0; k < ns; k++) {
+        const size_t W = (size_t)words(scenes[k].n_facets);
+        mout[k] = ptr<uint32_t>(c, S_TUNE_M) + om;
+        om += (size_t)scenes[k].n_facets * W;
+        tout[k] = ptr<uint32_t>(c, S_TUNE_T) + ot;
+        ot += (size_t)snaps[k] * 2 * W;
+        lout[k] = ptr<uint8_t>(c, S_TUNE_L) + ol;
+        ol += (size_t)snaps[k];
+    }
+    ivm_params base = *params;
+    base.flags &= ~IVM_FLAG_GRAPH;
+    const int wpbs[] = {2, 4};
+    const int mtiles[] = {1, 2, 4, 8, 16};
+    const int ttiles[] = {4, 8, 16, 32, 64};
+    float best_total = 1e30f;
+    ivm_params best = *params;
+    for (int wpb : wpbs) {
+        ivm_params p = base;
+        p.warps_per_block = wpb;
+        float bm = 0.f, bt = 0.f;
+        int mt = mtiles[0], tt = ttiles[0];
+        bool first = true;
+        for (int tile : mtiles) {
+            p.tile = tile;
+            ivm_stats st;
+            float ms = 1e30f;
+            for (int rep = 0; rep < 2; rep++) {   // the first run warms the arena up
+                if ((r = ivm_build_matrix(c, scenes, ns, &p, mout.data(), &st))) return r;
+                ms = st.ms_traverse;
+            }
+            if (first || ms < bm) { bm = ms; mt = tile; }
+            first = false;
+        }
+        p.tile = mt;
+        if (with_table) {
+            first = true;
+            for (int tile : ttiles) {
+                p.table_tile = tile;
+                ivm_stats st;
+                float ms = 1e30f;
+                for (int rep = 0; rep < 2; rep++) {
+                    if ((r = ivm_build_table(c, scenes, ns, &p, tx, rx, snaps.data(), tout.data(),
+                                             lout.data(), &st)))
+                        return r;
+                    ms = st.ms_traverse;
+                }
+                if (first || ms < bt) { bt = ms; tt = tile; }
+                first = false;
+            }
+            p.table_tile = tt;
+        }
+        if (bm + bt < best_total) {
+            best_total = bm + bt;
+            best = *params;
+            best.warps_per_block = wpb;
+            best.tile = mt;
+            if (with_table) best.table_tile = tt;
+        }
+    }
+    *params = best;
+    return IVM_OK;
 }

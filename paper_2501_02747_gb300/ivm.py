@@ -33,7 +33,8 @@ class ivm_scene(ctypes.Structure):
 class ivm_params(ctypes.Structure):
     _fields_ = [("samples_per_side", ctypes.c_int32), ("max_order", ctypes.c_int32),
                 ("mode", ctypes.c_int32), ("tile", ctypes.c_int32),
-                ("warps_per_block", ctypes.c_int32), ("flags", ctypes.c_int32)]
+                ("warps_per_block", ctypes.c_int32), ("flags", ctypes.c_int32),
+                ("table_tile", ctypes.c_int32)]
 
 
 class ivm_stats(ctypes.Structure):
@@ -73,6 +74,9 @@ SIGNATURES = {
                                ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
     "ivm_strerror": ([ctypes.c_int], ctypes.c_char_p),
     "ivm_kernel_launches": ([], ctypes.c_uint64),
+    "ivm_autotune": ([_VP, ctypes.POINTER(ivm_scene), ctypes.c_int32, ctypes.POINTER(_VP),
+                      ctypes.POINTER(_VP), ctypes.POINTER(ctypes.c_int64),
+                      ctypes.POINTER(ivm_params)], ctypes.c_int),
     "ivm_build_matrix_noalloc": ([_VP, ctypes.c_int32, ctypes.POINTER(ivm_params), _VP, _VP],
                                  ctypes.c_int),
 }
@@ -175,8 +179,34 @@ class Context:
         self.close()
 
 
-def _params(s, K=0, mode=IVM_MODE_EXACT, tile=0, warps_per_block=0, flags=0):
-    return ivm_params(s, K, mode, tile, warps_per_block, flags)
+def _params(s, K=0, mode=IVM_MODE_EXACT, tile=0, warps_per_block=0, flags=0, table_tile=0):
+    return ivm_params(s, K, mode, tile, warps_per_block, flags, table_tile)
+
+
+def ivm_autotune(ctx, facets, s, tx=None, rx=None, mode=IVM_MODE_FILTERED, flags=0):
+    """Launch shape for the given workload (one scene or a list): returns
+    dict(tile=..., warps_per_block=..., table_tile=...)."""
+    single = not isinstance(facets, (list, tuple))
+    flist = [facets] if single else list(facets)
+    scenes, keep = _scenes(flist)
+    p = _params(s, 0, mode, 0, 0, flags)
+    if tx is not None:
+        txs = [tx] if single else list(tx)
+        rxs = [rx] if single else list(rx)
+        conv = []
+        for a in txs + rxs:
+            conv.append(a if hasattr(a, "data_ptr")
+                        else np.ascontiguousarray(a, dtype=np.int32).reshape(-1, 3))
+        txs, rxs = conv[:len(txs)], conv[len(txs):]
+        n_snap = (ctypes.c_int64 * len(flist))(*[int(a.shape[0]) for a in txs])
+        tx_p = (_VP * len(flist))(*[_addr(a) for a in txs])
+        rx_p = (_VP * len(flist))(*[_addr(a) for a in rxs])
+        _check(lib().ivm_autotune(ctx.handle, scenes, len(flist), tx_p, rx_p, n_snap,
+                                  ctypes.byref(p)), "ivm_autotune")
+    else:
+        _check(lib().ivm_autotune(ctx.handle, scenes, len(flist), None, None, None,
+                                  ctypes.byref(p)), "ivm_autotune")
+    return {"tile": p.tile, "warps_per_block": p.warps_per_block, "table_tile": p.table_tile}
 
 
 def _scenes(facet_list):
@@ -251,7 +281,7 @@ def ivm_build_table(ctx, facets, s, tx, rx, mode=IVM_MODE_EXACT, flags=0, tile=0
     tx_p = (_VP * len(out))(*[_addr(a) for a in txs])
     rx_p = (_VP * len(out))(*[_addr(a) for a in rxs])
     st = ivm_stats()
-    p = _params(s, 0, mode, tile, warps_per_block, flags)
+    p = _params(s, 0, mode, 0, warps_per_block, flags, table_tile=tile)
     _check(lib().ivm_build_table(ctx.handle, scenes, len(flist), ctypes.byref(p), tx_p, rx_p,
                                  n_snap, tab_p, los_p, ctypes.byref(st)), "ivm_build_table")
     return (out[0] if single else out), st

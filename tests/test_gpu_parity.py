@@ -139,6 +139,27 @@ def test_graph_replay_rereads_inputs(ctx):
     assert ivm.kernel_launches() > l0   # replays are counted as launches
 
 
+def test_autotune_picks_a_valid_shape_and_results_stay_exact(ctx):
+    scenes = [sg.random_small_city(451 + k, n_buildings=4 + 2 * k, side=9000, n_snap=50, s=2)
+              for k in range(3)]
+    p = ivm.ivm_autotune(ctx, [sc.facets for sc in scenes], 2, [sc.tx for sc in scenes],
+                         [sc.rx for sc in scenes], flags=FAST)
+    assert p["warps_per_block"] in (2, 4)
+    assert p["tile"] in (1, 2, 4, 8, 16) and p["table_tile"] in (4, 8, 16, 32, 64)
+    for sc in scenes:
+        M, _ = ivm.ivm_build_matrix(ctx, sc.facets, 2, mode=ivm.IVM_MODE_FILTERED, flags=FAST,
+                                    tile=p["tile"], warps_per_block=p["warps_per_block"])
+        assert (to_np(M) == oracle.matrix(sc.facets, 2)).all()
+        (T, L), _ = ivm.ivm_build_table(ctx, sc.facets, 2, sc.tx, sc.rx,
+                                        mode=ivm.IVM_MODE_FILTERED, flags=FAST,
+                                        tile=p["table_tile"],
+                                        warps_per_block=p["warps_per_block"])
+        tab, los = oracle.table(sc.facets, 2, sc.tx, sc.rx)
+        assert (to_np(T) == tab).all() and (L.cpu().numpy() == los).all()
+    m_only = ivm.ivm_autotune(ctx, scenes[0].facets, 2, flags=FAST)
+    assert m_only["tile"] in (1, 2, 4, 8, 16)
+
+
 def test_many_samples_table_path(ctx):
     """s = 6 and 8: s*s > 32 samples per facet take several packets."""
     sc = sg.random_small_city(411, n_buildings=3, side=6000, n_snap=10, s=6)

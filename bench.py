@@ -236,12 +236,21 @@ def run_ours(args, ws, rank, local):
                      | ivm.IVM_FLAG_DEDUP_SOURCES | ivm.IVM_FLAG_GRAPH),
     }
 
+    forms["learned"] = dict(mode=ivm.IVM_MODE_LEARNED, flags=forms["fast"]["flags"])
+
     # launch shape of the fast form from the library's autotuner (untimed)
     tuned = ivm.ivm_autotune(ctx, facets_d, s, tx_d, rx_d, mode=forms["fast"]["mode"],
                              flags=forms["fast"]["flags"])
     shape = {"plain": ({}, {}),
              "fast": ({"tile": tuned["tile"], "warps_per_block": tuned["warps_per_block"]},
                       {"tile": tuned["table_tile"], "warps_per_block": tuned["warps_per_block"]})}
+    shape["learned"] = shape["fast"]
+    # the cluster ranker of the learned form, trained (untimed) on the exact
+    # method's logged hits in the tiny and degenerate scenes
+    t0 = time.perf_counter()
+    train_loss = ivm.ivm_ranker_train(ctx, [sg.tiny().facets, sg.degenerate(n_snap=16).facets],
+                                      s, epochs=12, lr=2e-3)
+    train_s = time.perf_counter() - t0
 
     def step(form, fac, tx, rx, M, T, L, summ, marks=None):
         """The three calls; `marks` (4 CUDA events) bracket them on the stream."""
@@ -319,12 +328,18 @@ def run_ours(args, ws, rank, local):
     clocks.start()
     ms_fast, kern_fast, ops_fast, launches, stats_fast, calls_fast = timed("fast")
     clk = clocks.stop()
+    ms_lrn, kern_lrn, _, _, stats_lrn, calls_lrn = timed("learned")
 
-    # parity of the two forms on this step's outputs (cheap, outside timing)
+    # parity of the forms on this step's outputs (cheap, outside timing)
     step("plain", facets_d, tx_d, rx_d, M_d, T_d, L_d, summ_d)
     ref = (M_d.clone(), T_d.clone(), L_d.clone(), summ_d.clone())
     step("fast", facets_d, tx_d, rx_d, M_d, T_d, L_d, summ_d)
     forms_agree = all(bool((a == b).all()) for a, b in zip(ref, (M_d, T_d, L_d, summ_d)))
+    step("learned", facets_d, tx_d, rx_d, M_d, T_d, L_d, summ_d)
+    forms_agree &= all(bool((a == b).all()) for a, b in zip(ref, (M_d, T_d, L_d, summ_d)))
+
+    def per_seg(st, key):
+        return st[key] / st["segments"] if st["segments"] else None
 
     value = ws * units / (ms_fast / 1e3)
     out = {
@@ -342,7 +357,21 @@ def run_ours(args, ws, rank, local):
         "plain": {"ms_per_step": ms_plain, "value": ws * units / (ms_plain / 1e3),
                   "form": "exact int64/int128 facet tests, one warp per work item"},
         "speedup_vs_plain": ms_plain / ms_fast,
-        "ms_per_call": {"fast": calls_fast, "plain": calls_plain},
+        "learned": {
+            "form": "fast + learned cluster order in the matrix call (BF16 MLP ranking of "
+                    "64 BVH subtrees per candidate pair, tensor-core inference)",
+            "ms_per_step": ms_lrn, "value": ws * units / (ms_lrn / 1e3),
+            "speedup_vs_plain": ms_plain / ms_lrn,
+            "matrix_ms_per_call": calls_lrn["matrix"],
+            "matrix_ms_per_call_without_ranker": calls_fast["matrix"],
+            "matrix_node_tests_per_segment": per_seg(stats_lrn[0], "node_tests"),
+            "matrix_node_tests_per_segment_without_ranker": per_seg(stats_fast[0], "node_tests"),
+            "matrix_leaf_tests_per_segment": per_seg(stats_lrn[0], "leaf_tests"),
+            "matrix_leaf_tests_per_segment_without_ranker": per_seg(stats_fast[0], "leaf_tests"),
+            "first_proposal_hits": stats_lrn[0]["ranker_hits"],
+            "train": {"scenes": "tiny (41 facets) + degenerate district (1,001 facets)",
+                      "epochs": 12, "final_loss": train_loss, "seconds": train_s}},
+        "ms_per_call": {"fast": calls_fast, "plain": calls_plain, "learned": calls_lrn},
         "forms_bit_identical": forms_agree,
         "gpu_launches": launches,
         "clocks": clk,

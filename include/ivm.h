@@ -171,6 +171,55 @@ int ivm_expand_image_tree(ivm_ctx *ctx, const uint32_t *matrix, const uint32_t *
                           int32_t max_order, ivm_tree_summary *summary, int32_t *paths,
                           int64_t path_capacity, int64_t *n_paths_out);
 
+/* ------------------------------------------------------------ learned form
+ * Not in the paper: a small MLP proposes, for each candidate facet pair, the
+ * order in which to walk the scene's 64 BVH clusters (64 contiguous ranges
+ * of the Morton-sorted facets), so that blocked sample segments meet their
+ * occluder early.  Inputs: the two facet centroids normalised to the scene
+ * box (6), both unit normals (6), and per cluster the entry depth of the
+ * centroid segment into the cluster's box (64).  Layers 76 -> 128 -> 128 ->
+ * 128 -> 64 with ReLU; inference in BF16 with FP32 accumulation on the
+ * tensor cores, training in FP32.  With IVM_MODE_LEARNED and a trained or
+ * loaded ranker, ivm_build_matrix walks the top proposals first (while they
+ * keep blocking lanes) and then the rest of the tree; every bit is still
+ * decided by the same exact facet tests, so results never depend on the
+ * weights.  Without weights IVM_MODE_LEARNED behaves as IVM_MODE_FILTERED.
+ *
+ * Master weights: IVM_RANKER_PARAMS floats, row-major W1[76][128], b1[128],
+ * W2[128][128], b2, W3[128][128], b3, W4[128][64], b4[64]. */
+#define IVM_RANKER_PARAMS 51136
+
+/* Train the ranker on the given scenes: for every candidate pair whose
+ * central-sample segment is blocked, the label is the cluster of the nearest
+ * facet it meets (logged by the exact traversal); weights are initialised
+ * from a fixed seed and trained by Adam (batch 512) for `epochs` epochs with
+ * step `lr`.  *final_loss (may be NULL) receives the mean cross-entropy of the
+ * last epoch.  Errors: as ivm_build_matrix; IVM_ERR_ARG if no pair is
+ * labelled. */
+int ivm_ranker_train(ivm_ctx *ctx, const ivm_scene *scenes, int32_t n_scenes,
+                     const ivm_params *params, int32_t epochs, float lr, float *final_loss);
+
+/* Serialise the ranker (header + master weights).  blob NULL: *bytes gets the
+ * size.  Errors: IVM_ERR_ARG (no ranker, or *bytes too small). */
+int ivm_ranker_save(ivm_ctx *ctx, void *blob, size_t *bytes);
+
+/* Load a ranker saved by ivm_ranker_save.  Errors: IVM_ERR_ARG (bad blob). */
+int ivm_ranker_load(ivm_ctx *ctx, const void *blob, size_t bytes);
+
+/* Run the loaded ranker's inference kernel (BF16 tensor cores, FP32
+ * accumulation) on feature rows x [batch][76] (host): logits [batch][64] and
+ * top [batch][8], the eight highest-scoring clusters per row in order (ties
+ * to the lower index); either output may be NULL.  For checking the kernel.
+ * Errors: IVM_ERR_ARG (no ranker, batch < 1, both outputs NULL). */
+int ivm_ranker_infer(ivm_ctx *ctx, const float *x, int32_t batch, float *logits, uint8_t *top);
+
+/* Mean softmax cross-entropy of a batch and its gradient with respect to the
+ * master weights, computed by the training kernels (host pointers): weights
+ * [IVM_RANKER_PARAMS], x [batch][76], y [batch] (0..63), grads
+ * [IVM_RANKER_PARAMS].  For checking the training kernels. */
+int ivm_ranker_gradients(ivm_ctx *ctx, const float *weights, const float *x, const int32_t *y,
+                         int32_t batch, float *grads, float *loss);
+
 /* Autotuner for the batched / persistent form (not in the paper: a launch
  * schedule choice).  Times candidate launch shapes on a sample of the given
  * workload -- the first 8 scenes at most and the first 16,384 snapshots of

@@ -97,6 +97,7 @@ __global__ void k_rank_sort(DevScenes g, unsigned long long *sorted)
     if (i < D.n) {
         sorted[D.facet0 + rank] = mine;
         g.order[D.facet0 + rank] = D.facet0 + (int)(mine & 0xffffffffu);
+        g.leaf[D.facet0 + (int)(mine & 0xffffffffu)].pad = rank;   // sorted position
     }
 }
 
@@ -151,7 +152,7 @@ __global__ void k_karras(DevScenes g, const unsigned long long *sorted)
         right = D.node0 + gam + 1;
         g.parent[g.total_facets + right] = (node << 1) | 1;
     }
-    g.nodes[node].d = make_int4(left, right, 0, 0);
+    g.nodes[node].d = make_int4(left, right, lo, hi);   // + the node's sorted range
     if (i == 0) g.parent[g.total_facets + node] = -1;
 }
 

@@ -9,12 +9,14 @@
 // stats).  The persistent form enqueues without any host synchronisation:
 // the matrix kernel reads the candidate-pair count from device memory and
 // the ingest range check is reported at the end.
+#include <algorithm>
 #include <atomic>
 #include <cstdio>
 #include <cstring>
 #include <vector>
 
 #include "ivm_internal.cuh"
+#include "ranker.cuh"
 #include "tree.cuh"
 
 using namespace ivm;
@@ -31,6 +33,7 @@ enum Slot {
     S_T_MAT, S_T_TAB, S_T_LOS, S_T_SUM, S_T_DEG, S_T_ROW, S_T_COL, S_T_WT, S_T_XA, S_T_XB,
     S_T_CNT, S_T_OFF, S_T_BS, S_T_BO, S_T_PATHS, S_T_FLAG, S_T_EXCL, S_T_RUN, S_T_START,
     S_TUNE_M, S_TUNE_T, S_TUNE_L,
+    S_CBOX, S_NCL, S_RANKS, S_RFEAT, S_RLAB, S_RIDX, S_RXB, S_RYB, S_RACT, S_RLOSS, S_RWT, S_RGT,
     S_COUNT
 };
 
@@ -70,6 +73,10 @@ struct ivm_ctx {
     std::vector<GraphEntry> graphs;
     unsigned long long uses = 0;
     cudaStream_t cap = nullptr;           // private stream used only for capture
+    // learned ranking: FP32 master weights, Adam moments, BF16 inference copy
+    float *r_master = nullptr, *r_m = nullptr, *r_v = nullptr, *r_grads = nullptr;
+    __nv_bfloat16 *r_wt = nullptr;
+    bool has_ranker = false;
 };
 
 namespace {
@@ -449,6 +456,9 @@ extern "C" int ivm_destroy(ivm_ctx *c)
     cudaStreamSynchronize(c->stream);
     for (auto &e : c->graphs) drop_graph(e);
     if (c->cap) cudaStreamDestroy(c->cap);
+    for (void *p : {(void *)c->r_master, (void *)c->r_m, (void *)c->r_v, (void *)c->r_grads,
+                    (void *)c->r_wt})
+        if (p) cudaFree(p);
     for (auto &b : c->buf)
         if (b.p) cudaFree(b.p);
     cudaFree(c->d_err);
@@ -491,6 +501,13 @@ extern "C" int ivm_build_matrix(ivm_ctx *c, const ivm_scene *scenes, int32_t n_s
     const LaunchCfg cfg0 = launch_cfg(c, params);
     const bool dev_count = cfg0.persistent && upper <= kDevCountMaxPairs;
     const bool use_graph = (params->flags & IVM_FLAG_GRAPH) && dev_count && all_device;
+    const bool learned = params->mode == IVM_MODE_LEARNED && c->has_ranker;
+    if (learned) {
+        if ((r = ensure(c, S_CBOX, sizeof(int) * kRCtx * (size_t)n_scenes))) return r;
+        if ((r = ensure(c, S_NCL, (size_t)g.total_nodes + 1))) return r;
+        if (dev_count && (r = ensure(c, S_RANKS, sizeof(unsigned long long) * (size_t)upper)))
+            return r;
+    }
     if ((r = ensure(c, S_OUT, sizeof(uint32_t) * host_words))) return r;
     if (dev_count && (r = ensure(c, S_PAIRS, sizeof(int2) * (size_t)upper))) return r;
     size_t off = 0;
@@ -522,6 +539,17 @@ extern "C" int ivm_build_matrix(ivm_ctx *c, const ivm_scene *scenes, int32_t n_s
             CK(cudaMemsetAsync(hd[k].matrix, 0, sizeof(uint32_t) * hd[k].n * hd[k].W, c->stream));
         LaunchCfg cfg = cfg0;
         cfg.count_dev = dev_count ? c->d_misc : nullptr;
+        if (learned) {   // rank the clusters of every candidate pair
+            if (!dev_count && (e = ensure(c, S_RANKS, sizeof(unsigned long long) * npairs)))
+                return e;
+            CK(ranker_clusters(g, ptr<int>(c, S_CBOX), ptr<signed char>(c, S_NCL), c->stream));
+            CK(ranker_rank_pairs(g, ptr<int2>(c, S_PAIRS), npairs, cfg.count_dev,
+                                 ptr<int>(c, S_CBOX), RankerDev{c->r_wt, c->r_master},
+                                 ptr<unsigned long long>(c, S_RANKS), c->n_sm, c->stream));
+            cfg.learn.ranks = ptr<unsigned long long>(c, S_RANKS);
+            cfg.learn.ctx = ptr<int>(c, S_CBOX);
+            cfg.learn.ncl = ptr<signed char>(c, S_NCL);
+        }
         CK(launch_matrix(g, ptr<int2>(c, S_PAIRS), npairs, cfg, c->d_misc + 2, c->d_ctr,
                          c->d_err, c->stream));
         CK(record(c, 4));
@@ -529,7 +557,8 @@ extern "C" int ivm_build_matrix(ivm_ctx *c, const ivm_scene *scenes, int32_t n_s
     };
     // ---- execute
     if (use_graph) {
-        std::vector<unsigned long long> key = {0ull, (unsigned long long)n_scenes};
+        std::vector<unsigned long long> key = {0ull, (unsigned long long)n_scenes,
+                                               (unsigned long long)learned};
         key_params(key, params);
         for (int k = 0; k < n_scenes; k++) {
             key.push_back((unsigned long long)(uintptr_t)scenes[k].facets);
@@ -841,6 +870,234 @@ extern "C" int ivm_expand_image_tree(ivm_ctx *c, const uint32_t *matrix, const u
         *n_paths_out = tot;
     }
     return status;
+}
+
+// ============================================================================ ranker
+
+namespace {
+
+struct RankerHeader {
+    uint32_t magic, version, in, hidden, out, params;
+};
+constexpr uint32_t kRankerMagic = 0x524d5649u;   // "IVMR"
+
+int ranker_alloc(ivm_ctx *c)
+{
+    if (c->r_master) return IVM_OK;
+    CK(cudaMalloc(&c->r_master, sizeof(float) * kRParams));
+    CK(cudaMalloc(&c->r_m, sizeof(float) * kRParams));
+    CK(cudaMalloc(&c->r_v, sizeof(float) * kRParams));
+    CK(cudaMalloc(&c->r_grads, sizeof(float) * kRParams));
+    CK(cudaMalloc(&c->r_wt, sizeof(__nv_bfloat16) * kRTEnd));
+    return IVM_OK;
+}
+
+uint64_t sm64(uint64_t &state)
+{
+    uint64_t z = (state += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// He-uniform initial weights from a fixed SplitMix64 stream, zero biases
+void ranker_init(std::vector<float> &w)
+{
+    w.assign(kRParams, 0.f);
+    uint64_t st = 0x1D0E5EEDull;
+    const int lay[4][3] = {{kRIn, kRH, kRW1}, {kRH, kRH, kRW2}, {kRH, kRH, kRW3}, {kRH, kROut, kRW4}};
+    for (auto &L : lay) {
+        const float bound = sqrtf(6.f / L[0]);
+        for (int i = 0; i < L[0] * L[1]; i++) {
+            const float u = (float)(sm64(st) >> 11) * (1.f / 9007199254740992.f);
+            w[L[2] + i] = (2.f * u - 1.f) * bound;
+        }
+    }
+}
+
+}  // namespace
+
+extern "C" int ivm_ranker_train(ivm_ctx *c, const ivm_scene *scenes, int32_t n_scenes,
+                                const ivm_params *params, int32_t epochs, float lr,
+                                float *final_loss)
+{
+    if (!c || epochs < 1 || !(lr > 0.f)) return IVM_ERR_ARG;
+    int r = check_params(params);
+    if (r) return r;
+    DeviceGuard dg(c->device);
+    // candidate pairs and their logged nearest occluders
+    DevScenes g;
+    std::vector<SceneDesc> hd;
+    if ((r = plan_geometry(c, scenes, n_scenes, params->samples_per_side, g, hd))) return r;
+    if ((r = ensure(c, S_CBOX, sizeof(int) * kRCtx * (size_t)n_scenes))) return r;
+    if ((r = ensure(c, S_NCL, (size_t)g.total_nodes + 1))) return r;
+    bind_geometry(c, g);
+    if ((r = enqueue_geometry(c, g, scenes, hd, hd.data(), true))) return r;
+    CK(cudaMemsetAsync(c->d_misc, 0, sizeof(unsigned long long) * 2, c->stream));
+    CK(launch_screen_count(g, hd.data(), c->d_misc, c->stream));
+    CK(cudaMemcpyAsync(c->h_misc, c->d_misc, sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                       c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    const unsigned long long npairs = c->h_misc[0];
+    if (npairs == 0) return IVM_ERR_ARG;
+    if ((r = ensure(c, S_PAIRS, sizeof(int2) * npairs))) return r;
+    if ((r = ensure(c, S_RFEAT, sizeof(float) * kRInPad * npairs))) return r;
+    if ((r = ensure(c, S_RLAB, sizeof(int) * npairs))) return r;
+    bind_geometry(c, g);
+    CK(launch_screen_emit(g, hd.data(), ptr<int2>(c, S_PAIRS), c->d_misc + 1, npairs, c->stream));
+    CK(ranker_clusters(g, ptr<int>(c, S_CBOX), ptr<signed char>(c, S_NCL), c->stream));
+    CK(ranker_log_hits(g, ptr<int2>(c, S_PAIRS), npairs, ptr<int>(c, S_CBOX),
+                       ptr<float>(c, S_RFEAT), ptr<int>(c, S_RLAB), nullptr, npairs, c->d_err,
+                       c->stream));
+    if ((r = read_error(c))) return r;
+    std::vector<int> lab(npairs);
+    std::vector<int2> prs(npairs);
+    CK(cudaMemcpy(lab.data(), ptr<int>(c, S_RLAB), sizeof(int) * npairs, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(prs.data(), ptr<int2>(c, S_PAIRS), sizeof(int2) * npairs,
+                  cudaMemcpyDeviceToHost));
+    std::vector<int> idx;
+    for (unsigned long long i = 0; i < npairs; i++)
+        if (lab[i] >= 0) idx.push_back((int)i);
+    if (idx.empty()) return IVM_ERR_ARG;
+    // the screen emits pairs in atomic order: sort by pair so that the
+    // shuffled batches, and so the trained weights, are reproducible
+    std::sort(idx.begin(), idx.end(), [&](int a, int b) {
+        return prs[a].x != prs[b].x ? prs[a].x < prs[b].x : prs[a].y < prs[b].y;
+    });
+    // weights and optimiser state
+    if ((r = ranker_alloc(c))) return r;
+    std::vector<float> w;
+    ranker_init(w);
+    CK(cudaMemcpy(c->r_master, w.data(), sizeof(float) * kRParams, cudaMemcpyHostToDevice));
+    CK(cudaMemset(c->r_m, 0, sizeof(float) * kRParams));
+    CK(cudaMemset(c->r_v, 0, sizeof(float) * kRParams));
+    const int B = 512;
+    const int n = (int)idx.size();
+    const int steps = (n + B - 1) / B;
+    if ((r = ensure(c, S_RIDX, sizeof(int) * (size_t)n))) return r;
+    if ((r = ensure(c, S_RXB, sizeof(float) * B * kRIn))) return r;
+    if ((r = ensure(c, S_RYB, sizeof(int) * B))) return r;
+    if ((r = ensure(c, S_RACT, sizeof(float) * ranker_act_floats(B)))) return r;
+    if ((r = ensure(c, S_RLOSS, sizeof(float) * (size_t)steps))) return r;
+    uint64_t shuffle = 0xC0FFEEull;
+    int step = 0;
+    for (int ep = 0; ep < epochs; ep++) {
+        for (int i = n - 1; i > 0; i--) {   // Fisher-Yates with a fixed stream
+            const int j = (int)(sm64(shuffle) % (uint64_t)(i + 1));
+            std::swap(idx[i], idx[j]);
+        }
+        CK(cudaMemcpyAsync(ptr<int>(c, S_RIDX), idx.data(), sizeof(int) * n,
+                           cudaMemcpyHostToDevice, c->stream));
+        for (int b = 0; b < steps; b++) {
+            const int bb = b * B + B <= n ? B : n - b * B;
+            CK(ranker_gather(ptr<float>(c, S_RFEAT), ptr<int>(c, S_RLAB), ptr<int>(c, S_RIDX) + b * B,
+                             bb, ptr<float>(c, S_RXB), ptr<int>(c, S_RYB), c->stream));
+            CK(ranker_grad(c->r_master, ptr<float>(c, S_RXB), ptr<int>(c, S_RYB), bb,
+                           ptr<float>(c, S_RACT), c->r_grads, ptr<float>(c, S_RLOSS) + b, c->stream));
+            CK(ranker_adam(c->r_master, c->r_grads, c->r_m, c->r_v, lr, ++step, c->stream));
+        }
+        CK(cudaStreamSynchronize(c->stream));   // the index buffer is rewritten next epoch
+    }
+    std::vector<float> losses(steps);
+    CK(cudaMemcpy(losses.data(), ptr<float>(c, S_RLOSS), sizeof(float) * steps,
+                  cudaMemcpyDeviceToHost));
+    double sum = 0.0;
+    for (float l : losses) sum += l;
+    if (final_loss) *final_loss = (float)(sum / steps);
+    CK(ranker_pack(c->r_master, c->r_wt, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    c->has_ranker = true;
+    return IVM_OK;
+}
+
+extern "C" int ivm_ranker_save(ivm_ctx *c, void *blob, size_t *bytes)
+{
+    if (!c || !bytes || !c->has_ranker) return IVM_ERR_ARG;
+    const size_t need = sizeof(RankerHeader) + sizeof(float) * kRParams;
+    if (!blob) {
+        *bytes = need;
+        return IVM_OK;
+    }
+    if (*bytes < need) return IVM_ERR_ARG;
+    DeviceGuard dg(c->device);
+    RankerHeader h = {kRankerMagic, 1u, (uint32_t)kRIn, (uint32_t)kRH, (uint32_t)kROut,
+                      (uint32_t)kRParams};
+    memcpy(blob, &h, sizeof h);
+    CK(cudaMemcpy(static_cast<char *>(blob) + sizeof h, c->r_master, sizeof(float) * kRParams,
+                  cudaMemcpyDeviceToHost));
+    *bytes = need;
+    return IVM_OK;
+}
+
+extern "C" int ivm_ranker_load(ivm_ctx *c, const void *blob, size_t bytes)
+{
+    if (!c || !blob || bytes != sizeof(RankerHeader) + sizeof(float) * kRParams) return IVM_ERR_ARG;
+    RankerHeader h;
+    memcpy(&h, blob, sizeof h);
+    if (h.magic != kRankerMagic || h.version != 1u || h.in != (uint32_t)kRIn ||
+        h.hidden != (uint32_t)kRH || h.out != (uint32_t)kROut || h.params != (uint32_t)kRParams)
+        return IVM_ERR_ARG;
+    DeviceGuard dg(c->device);
+    int r;
+    if ((r = ranker_alloc(c))) return r;
+    CK(cudaMemcpy(c->r_master, static_cast<const char *>(blob) + sizeof h,
+                  sizeof(float) * kRParams, cudaMemcpyHostToDevice));
+    CK(ranker_pack(c->r_master, c->r_wt, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    c->has_ranker = true;
+    return IVM_OK;
+}
+
+extern "C" int ivm_ranker_infer(ivm_ctx *c, const float *x, int32_t batch, float *logits,
+                                uint8_t *top)
+{
+    if (!c || !x || batch < 1 || (!logits && !top) || !c->has_ranker) return IVM_ERR_ARG;
+    DeviceGuard dg(c->device);
+    int r;
+    if ((r = ensure(c, S_RXB, sizeof(float) * (size_t)batch * kRIn))) return r;
+    if ((r = ensure(c, S_RACT, sizeof(float) * (size_t)batch * kROut))) return r;
+    if ((r = ensure(c, S_RANKS, sizeof(unsigned long long) * (size_t)batch))) return r;
+    CK(cudaMemcpyAsync(ptr<float>(c, S_RXB), x, sizeof(float) * (size_t)batch * kRIn,
+                       cudaMemcpyHostToDevice, c->stream));
+    CK(ranker_infer(ptr<float>(c, S_RXB), (unsigned long long)batch, RankerDev{c->r_wt, c->r_master},
+                    ptr<float>(c, S_RACT), ptr<unsigned long long>(c, S_RANKS), c->n_sm, c->stream));
+    if (logits)
+        CK(cudaMemcpyAsync(logits, ptr<float>(c, S_RACT), sizeof(float) * (size_t)batch * kROut,
+                           cudaMemcpyDeviceToHost, c->stream));
+    if (top)
+        CK(cudaMemcpyAsync(top, ptr<unsigned long long>(c, S_RANKS),
+                           sizeof(unsigned long long) * (size_t)batch, cudaMemcpyDeviceToHost,
+                           c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return IVM_OK;
+}
+
+extern "C" int ivm_ranker_gradients(ivm_ctx *c, const float *weights, const float *x,
+                                    const int32_t *y, int32_t batch, float *grads, float *loss)
+{
+    if (!c || !weights || !x || !y || !grads || !loss || batch < 1) return IVM_ERR_ARG;
+    for (int i = 0; i < batch; i++)
+        if (y[i] < 0 || y[i] >= kROut) return IVM_ERR_ARG;
+    DeviceGuard dg(c->device);
+    int r;
+    if ((r = ensure(c, S_RWT, sizeof(float) * kRParams))) return r;
+    if ((r = ensure(c, S_RGT, sizeof(float) * (kRParams + 1)))) return r;
+    if ((r = ensure(c, S_RXB, sizeof(float) * (size_t)batch * kRIn))) return r;
+    if ((r = ensure(c, S_RYB, sizeof(int) * (size_t)batch))) return r;
+    if ((r = ensure(c, S_RACT, sizeof(float) * ranker_act_floats(batch)))) return r;
+    CK(cudaMemcpyAsync(ptr<float>(c, S_RWT), weights, sizeof(float) * kRParams,
+                       cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(ptr<float>(c, S_RXB), x, sizeof(float) * (size_t)batch * kRIn,
+                       cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(ptr<int>(c, S_RYB), y, sizeof(int) * (size_t)batch, cudaMemcpyHostToDevice,
+                       c->stream));
+    float *g = ptr<float>(c, S_RGT);
+    CK(ranker_grad(ptr<float>(c, S_RWT), ptr<float>(c, S_RXB), ptr<int>(c, S_RYB), batch,
+                   ptr<float>(c, S_RACT), g, g + kRParams, c->stream));
+    CK(cudaMemcpyAsync(grads, g, sizeof(float) * kRParams, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(loss, g + kRParams, sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return IVM_OK;
 }
 
 // ============================================================================ autotuner

@@ -25,7 +25,7 @@ struct __align__(16) Leaf {
     int ox, oy, oz, building;   // origin O = 2s o
     int ux, uy, uz, scene;      // edge U = 2s u
     int vx, vy, vz, dom;        // edge V = 2s v; dom = dominant axis of n
-    int nx, ny, nz, pad;        // reduced outward normal
+    int nx, ny, nz, pad;        // reduced outward normal; pad = Morton-sorted position
 };
 
 // Internal BVH node: the boxes of both children (closed, float holding exact
@@ -36,7 +36,7 @@ struct __align__(16) Node {
     float4 a;   // lo_L.x lo_L.y lo_L.z hi_L.x
     float4 b;   // hi_L.y hi_L.z lo_R.x lo_R.y
     float4 c;   // lo_R.z hi_R.x hi_R.y hi_R.z
-    int4 d;     // child_L child_R parent unused
+    int4 d;     // child_L child_R; first and last Morton-sorted position covered
 };
 
 // Per-scene descriptor (device copy).
@@ -111,6 +111,14 @@ cudaError_t launch_screen_emit(const DevScenes &g, const SceneDesc *host_desc, i
                                cudaStream_t st);
 
 // Launch shape of the traversal kernels.
+// Learned form: per candidate pair the top-8 proposed clusters (one byte
+// each, best first), the per-scene cluster context and the cut-node marks.
+struct LearnedDev {
+    const unsigned long long *ranks = nullptr;
+    const int *ctx = nullptr;
+    const signed char *ncl = nullptr;
+};
+
 struct LaunchCfg {
     int mode;             // IVM_MODE_*
     int persistent;       // work queue over a grid of n_sm * blocks_per_sm blocks
@@ -120,6 +128,7 @@ struct LaunchCfg {
     int cache;            // occluder cache in front of the BVH walk
     int dedup;            // table: compute one row per run of equal source positions
     const unsigned long long *count_dev = nullptr;  // matrix, persistent: device pair count
+    LearnedDev learn;     // matrix, learned form (ranks == nullptr: off)
 };
 
 cudaError_t launch_matrix(const DevScenes &g, const int2 *pairs, unsigned long long npairs,

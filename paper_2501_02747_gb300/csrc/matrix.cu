@@ -10,15 +10,67 @@
 // pairs 32 at a time as a packet; a packet ends as soon as every lane is
 // blocked, and the pair ends at the first packet with a free lane.  The bit
 // is written to row i and, by symmetry, row j.
+//
+// Learned form: the pair's ranked clusters (ranker.cu) are walked first, in
+// order, while they keep blocking lanes; then the rest of the tree without
+// them.  The set of facets tested is the same as in a full walk, so the bit
+// is the same.
 #include "ivm_internal.cuh"
 #include "traverse.cuh"
 #include "filter.cuh"
+#include "ranker.cuh"
 
 namespace ivm {
 
+// Proposals walked at most before the rest of the tree.
+constexpr int kRankedWalks = 8;
+
+// Cluster-first walk of a packet; same contract as occlude().
 template <bool CACHE, class LeafFn>
-__device__ __forceinline__ void decide_pair(const DevScenes &g, int gi, int gj, int *err,
-                                            WalkCounters &wc, LeafFn leaf, OccluderCache &cache)
+__device__ __forceinline__ unsigned occlude_ranked(Seg &s, unsigned alive, const Node *nodes,
+                                                   const Leaf *leaves, int root,
+                                                   const int *C, const signed char *ncl,
+                                                   unsigned long long rk, float dirx, float diry,
+                                                   float dirz, int budget, int *err,
+                                                   WalkCounters &wc, LeafFn leaf_hit,
+                                                   OccluderCache &cache, int &myblk)
+{
+    const int lane = threadIdx.x & 31;
+    if (CACHE) {
+        alive = cache_tests(s, alive, leaves, wc, leaf_hit, cache, myblk);
+        if (!alive) return 0;
+    }
+    if (s.ix == 0.f) finish_seg(s);
+    unsigned long long done = 0;
+    int blocker, last = -1;
+    for (int k = 0; k < kRankedWalks && k < kRTop; k++) {
+        const int c = (int)((rk >> (8 * k)) & 0xff);
+        if (c >= kRClusters || ((done >> c) & 1ull)) continue;
+        if (__ldg(C + kRCStart + c + 1) <= __ldg(C + kRCStart + c)) continue;   // empty
+        const unsigned before = alive;
+        alive = walk_packet(s, alive, nodes, leaves, __ldg(C + kRCut + c), dirx, diry, dirz,
+                            budget, err, wc, leaf_hit, blocker, myblk);
+        done |= 1ull << c;
+        if (blocker >= 0) last = blocker;
+        if (k == 0) wc.ranker_hits += ((before & ~alive) >> lane) & 1u;
+        if (!alive) {
+            if (CACHE) cache.put(last);
+            return 0;
+        }
+        if (alive == before) break;   // the proposal blocked nothing: stop trusting it
+    }
+    alive = walk_packet(s, alive, nodes, leaves, root, dirx, diry, dirz, budget, err, wc,
+                        leaf_hit, blocker, myblk, CutFilter{ncl, done});
+    if (blocker >= 0) last = blocker;
+    if (CACHE) cache.put(last);
+    return alive;
+}
+
+template <bool CACHE, bool LEARN, class LeafFn>
+__device__ __forceinline__ void decide_pair(const DevScenes &g, int gi, int gj,
+                                            const LearnedDev &lrn, unsigned long long rk,
+                                            int *err, WalkCounters &wc, LeafFn leaf,
+                                            OccluderCache &cache)
 {
     const int lane = threadIdx.x & 31;
     const Leaf Li = load_leaf(g.leaf, gi), Lj = load_leaf(g.leaf, gj);
@@ -47,8 +99,13 @@ __device__ __forceinline__ void decide_pair(const DevScenes &g, int gi, int gj, 
         wc.segments += face;
         Seg sg = make_seg(px, py, pz, qx, qy, qz);
         int myblk = -1;
-        alive = occlude<CACHE>(sg, alive, g.nodes, g.leaf, D.root, dirx, diry, dirz, budget, err,
-                               wc, leaf, cache, myblk);
+        if (LEARN)
+            alive = occlude_ranked<CACHE>(sg, alive, g.nodes, g.leaf, D.root,
+                                          lrn.ctx + (size_t)kRCtx * Li.scene, lrn.ncl, rk, dirx,
+                                          diry, dirz, budget, err, wc, leaf, cache, myblk);
+        else
+            alive = occlude<CACHE>(sg, alive, g.nodes, g.leaf, D.root, dirx, diry, dirz, budget,
+                                   err, wc, leaf, cache, myblk);
         if (alive) {
             visible = true;
             break;
@@ -60,11 +117,11 @@ __device__ __forceinline__ void decide_pair(const DevScenes &g, int gi, int gj, 
     }
 }
 
-template <bool PERSIST, bool CACHE, class LeafFn>
+template <bool PERSIST, bool CACHE, bool LEARN, class LeafFn>
 __global__ void __launch_bounds__(kTravThreads, IVM_MIN_BLOCKS)
 k_matrix(DevScenes g, const int2 *pairs, unsigned long long npairs, int tile,
-         const unsigned long long *count_dev, unsigned long long *work, unsigned long long *ctr,
-         int *err)
+         const unsigned long long *count_dev, LearnedDev lrn, unsigned long long *work,
+         unsigned long long *ctr, int *err)
 {
     WalkCounters wc;
     LeafFn leaf;
@@ -77,7 +134,8 @@ k_matrix(DevScenes g, const int2 *pairs, unsigned long long npairs, int tile,
         unsigned long long w = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
         if (w < npairs) {
             const int2 p = pairs[w];
-            decide_pair<CACHE>(g, p.x, p.y, err, wc, leaf, cache);
+            decide_pair<CACHE, LEARN>(g, p.x, p.y, lrn, LEARN ? lrn.ranks[w] : 0ull, err, wc,
+                                      leaf, cache);
         }
     } else {
         for (;;) {
@@ -88,44 +146,46 @@ k_matrix(DevScenes g, const int2 *pairs, unsigned long long npairs, int tile,
             unsigned long long end = min(base + (unsigned long long)tile, npairs);
             for (unsigned long long w = base; w < end; w++) {
                 const int2 p = pairs[w];
-                decide_pair<CACHE>(g, p.x, p.y, err, wc, leaf, cache);
+                decide_pair<CACHE, LEARN>(g, p.x, p.y, lrn, LEARN ? lrn.ranks[w] : 0ull, err,
+                                          wc, leaf, cache);
             }
         }
     }
     flush_counters(wc, ctr);
 }
 
-template <bool PERSIST, bool CACHE, class LeafFn>
+template <bool PERSIST, bool CACHE, bool LEARN, class LeafFn>
 static void launch_one(const DevScenes &g, const int2 *pairs, unsigned long long npairs,
                        const LaunchCfg &cfg, unsigned long long *work, unsigned long long *ctr,
                        int *err, cudaStream_t st)
 {
     const int threads = 32 * cfg.warps_per_block;
-    auto kern = k_matrix<PERSIST, CACHE, LeafFn>;
+    auto kern = k_matrix<PERSIST, CACHE, LEARN, LeafFn>;
     if (PERSIST) {
         int per_sm = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, 0);
         int blocks = cfg.n_sm * (per_sm > 0 ? per_sm : 1);
         cudaMemsetAsync(work, 0, sizeof(unsigned long long), st);
-        kern<<<blocks, threads, 0, st>>>(g, pairs, npairs, cfg.tile, cfg.count_dev, work, ctr,
-                                         err);
+        kern<<<blocks, threads, 0, st>>>(g, pairs, npairs, cfg.tile, cfg.count_dev, cfg.learn,
+                                         work, ctr, err);
     } else {
         unsigned long long blocks = (npairs + cfg.warps_per_block - 1) / cfg.warps_per_block;
-        kern<<<(unsigned)blocks, threads, 0, st>>>(g, pairs, npairs, 1, nullptr, work, ctr, err);
+        kern<<<(unsigned)blocks, threads, 0, st>>>(g, pairs, npairs, 1, nullptr, cfg.learn, work,
+                                                   ctr, err);
     }
 }
 
-template <class LeafFn>
+template <class LeafFn, bool LEARN>
 static void launch_leaf(const DevScenes &g, const int2 *pairs, unsigned long long npairs,
                         const LaunchCfg &cfg, unsigned long long *work, unsigned long long *ctr,
                         int *err, cudaStream_t st)
 {
     if (cfg.persistent) {
-        if (cfg.cache) launch_one<true, true, LeafFn>(g, pairs, npairs, cfg, work, ctr, err, st);
-        else launch_one<true, false, LeafFn>(g, pairs, npairs, cfg, work, ctr, err, st);
+        if (cfg.cache) launch_one<true, true, LEARN, LeafFn>(g, pairs, npairs, cfg, work, ctr, err, st);
+        else launch_one<true, false, LEARN, LeafFn>(g, pairs, npairs, cfg, work, ctr, err, st);
     } else {
-        if (cfg.cache) launch_one<false, true, LeafFn>(g, pairs, npairs, cfg, work, ctr, err, st);
-        else launch_one<false, false, LeafFn>(g, pairs, npairs, cfg, work, ctr, err, st);
+        if (cfg.cache) launch_one<false, true, LEARN, LeafFn>(g, pairs, npairs, cfg, work, ctr, err, st);
+        else launch_one<false, false, LEARN, LeafFn>(g, pairs, npairs, cfg, work, ctr, err, st);
     }
 }
 
@@ -134,8 +194,12 @@ cudaError_t launch_matrix(const DevScenes &g, const int2 *pairs, unsigned long l
                           unsigned long long *ctr, int *err, cudaStream_t st)
 {
     if (npairs == 0) return cudaSuccess;
-    if (cfg.mode == IVM_MODE_EXACT) launch_leaf<ExactLeaf>(g, pairs, npairs, cfg, work, ctr, err, st);
-    else launch_leaf<FilteredLeaf>(g, pairs, npairs, cfg, work, ctr, err, st);
+    if (cfg.mode == IVM_MODE_EXACT)
+        launch_leaf<ExactLeaf, false>(g, pairs, npairs, cfg, work, ctr, err, st);
+    else if (cfg.learn.ranks)
+        launch_leaf<FilteredLeaf, true>(g, pairs, npairs, cfg, work, ctr, err, st);
+    else
+        launch_leaf<FilteredLeaf, false>(g, pairs, npairs, cfg, work, ctr, err, st);
     note_launches(1);
     return cudaGetLastError();
 }

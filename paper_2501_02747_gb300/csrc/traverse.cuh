@@ -180,7 +180,7 @@ __device__ __forceinline__ Leaf load_leaf(const Leaf *leaves, int g)
 // A lane does far fewer than 2^32 tests in one launch.
 struct WalkCounters {
     unsigned node_tests = 0, leaf_tests = 0, undecided = 0, exact = 0, segments = 0,
-             cache_hits = 0;
+             cache_hits = 0, ranker_hits = 0;
 };
 
 // Traversal kernels run 128-thread blocks; the minimum-blocks hint caps
@@ -201,9 +201,11 @@ __device__ __forceinline__ void flush_counters(const WalkCounters &wc, unsigned 
 {
     unsigned long long a = warp_sum(wc.node_tests), b = warp_sum(wc.leaf_tests),
                        c = warp_sum(wc.undecided), d = warp_sum(wc.exact),
-                       e = warp_sum(wc.segments), f = warp_sum(wc.cache_hits);
+                       e = warp_sum(wc.segments), f = warp_sum(wc.cache_hits),
+                       h = warp_sum(wc.ranker_hits);
     if ((threadIdx.x & 31) == 0) {
         if (f) atomicAdd(ctr + C_CACHE_HITS, f);
+        if (h) atomicAdd(ctr + C_RANKER_HITS, h);
         if (a) atomicAdd(ctr + C_NODE_TESTS, a);
         if (b) atomicAdd(ctr + C_LEAF_TESTS, b);
         if (c) atomicAdd(ctr + C_UNDECIDED, c);
@@ -218,12 +220,19 @@ __device__ __forceinline__ void flush_counters(const WalkCounters &wc, unsigned 
 // (dirx, diry, dirz) is a packet direction used to visit the nearer child
 // first.  `budget` bounds the number of steps (a valid tree needs at most
 // 2 * nodes + 2); when it runs out, IVM_ERR_TIMEOUT is raised.
-template <class LeafFn>
+// `root` may be any node (or ~facet), so a walk can cover one subtree.
+// Walk filters: filt.node(index) says whether the walk enters an internal
+// node; NoFilter enters every node.
+struct NoFilter {
+    __device__ __forceinline__ bool node(int) const { return true; }
+};
+
+template <class LeafFn, class Filter = NoFilter>
 __device__ __forceinline__ unsigned walk_packet(const Seg &s, unsigned alive, const Node *nodes,
                                                 const Leaf *leaves, int root, float dirx,
                                                 float diry, float dirz, int budget, int *err,
                                                 WalkCounters &wc, LeafFn leaf_hit, int &blocker,
-                                                int &myblk)
+                                                int &myblk, Filter filt = Filter())
 {
     const int lane = threadIdx.x & 31;
     int s0 = 0, s1 = 0, sp = 0;   // stack: entry k lives in lane k&31 of s0 / s1
@@ -248,7 +257,7 @@ __device__ __forceinline__ unsigned walk_packet(const Seg &s, unsigned alive, co
             const float4 *np = reinterpret_cast<const float4 *>(nodes + node);
             float4 A = __ldg(np), B = __ldg(np + 1), C = __ldg(np + 2);
             int4 D = __ldg(reinterpret_cast<const int4 *>(np + 3));
-            bool me = (alive >> lane) & 1u;
+            bool me = ((alive >> lane) & 1u) && filt.node(node);
             bool hl = me && seg_box(s, A.x, A.y, A.z, A.w, B.x, B.y);
             bool hr = me && seg_box(s, B.z, B.w, C.x, C.y, C.z, C.w);
             wc.node_tests += 2 * me;
@@ -324,30 +333,40 @@ struct OccluderCache {
 // Lanes of the packet left unblocked: cached occluders first (when `cache`),
 // then the BVH walk.  Same contract as walk_packet; `myblk` receives, in each
 // lane that gets blocked, the facet that blocked it.
+// The warp's recently used occluders, tested before any walk.
+template <class LeafFn>
+__device__ __forceinline__ unsigned cache_tests(const Seg &s, unsigned alive, const Leaf *leaves,
+                                                WalkCounters &wc, LeafFn leaf_hit,
+                                                OccluderCache &cache, int &myblk)
+{
+    const int lane = threadIdx.x & 31;
+    int promote = -1;
+#pragma unroll
+    for (int k = 0; k < kCacheSize; k++) {
+        const int g = cache.f[k];
+        if (!alive || g < 0) break;
+        const Leaf L = load_leaf(leaves, g);
+        bool me = (alive >> lane) & 1u;
+        bool hit = me && leaf_hit(s, L, wc);
+        wc.leaf_tests += me;
+        wc.cache_hits += hit;
+        if (hit) myblk = g;
+        const unsigned hm = __ballot_sync(kFull, hit);
+        alive &= ~hm;
+        if (hm && k > 0 && promote < 0) promote = g;
+    }
+    if (promote >= 0) cache.put(promote);   // the facet that worked moves to the front
+    return alive;
+}
+
 template <bool CACHE, class LeafFn, bool LRU = CACHE>
 __device__ __forceinline__ unsigned occlude(Seg &s, unsigned alive, const Node *nodes,
                                             const Leaf *leaves, int root, float dirx, float diry,
                                             float dirz, int budget, int *err, WalkCounters &wc,
                                             LeafFn leaf_hit, OccluderCache &cache, int &myblk)
 {
-    const int lane = threadIdx.x & 31;
     if (CACHE && LRU) {
-        int promote = -1;
-#pragma unroll
-        for (int k = 0; k < kCacheSize; k++) {
-            const int g = cache.f[k];
-            if (!alive || g < 0) break;
-            const Leaf L = load_leaf(leaves, g);
-            bool me = (alive >> lane) & 1u;
-            bool hit = me && leaf_hit(s, L, wc);
-            wc.leaf_tests += me;
-            wc.cache_hits += hit;
-            if (hit) myblk = g;
-            const unsigned hm = __ballot_sync(kFull, hit);
-            alive &= ~hm;
-            if (hm && k > 0 && promote < 0) promote = g;
-        }
-        if (promote >= 0) cache.put(promote);   // the facet that worked moves to the front
+        alive = cache_tests(s, alive, leaves, wc, leaf_hit, cache, myblk);
         if (!alive) return 0;
     }
     int blocker;

@@ -81,6 +81,67 @@ SIGNATURES = {
                                  ctypes.c_int),
 }
 
+SIGNATURES.update({
+    "ivm_ranker_train": ([_VP, ctypes.POINTER(ivm_scene), ctypes.c_int32,
+                          ctypes.POINTER(ivm_params), ctypes.c_int32, ctypes.c_float,
+                          ctypes.POINTER(ctypes.c_float)], ctypes.c_int),
+    "ivm_ranker_save": ([_VP, _VP, ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
+    "ivm_ranker_load": ([_VP, _VP, ctypes.c_size_t], ctypes.c_int),
+    "ivm_ranker_gradients": ([_VP, _VP, _VP, _VP, ctypes.c_int32, _VP, _VP], ctypes.c_int),
+    "ivm_ranker_infer": ([_VP, _VP, ctypes.c_int32, _VP, _VP], ctypes.c_int),
+})
+
+RANKER_PARAMS, RANKER_IN, RANKER_HIDDEN, RANKER_OUT = 51136, 76, 128, 64
+
+
+def ivm_ranker_train(ctx, facets, s, epochs=8, lr=1e-3, mode=IVM_MODE_FILTERED):
+    """Train the cluster ranker on one scene or a list; returns the last epoch's loss."""
+    flist = list(facets) if isinstance(facets, (list, tuple)) else [facets]
+    scenes, keep = _scenes(flist)
+    p = _params(s, 0, mode)
+    loss = ctypes.c_float(0.0)
+    _check(lib().ivm_ranker_train(ctx.handle, scenes, len(flist), ctypes.byref(p), int(epochs),
+                                  float(lr), ctypes.byref(loss)), "ivm_ranker_train")
+    return float(loss.value)
+
+
+def ivm_ranker_save(ctx) -> bytes:
+    n = ctypes.c_size_t(0)
+    _check(lib().ivm_ranker_save(ctx.handle, None, ctypes.byref(n)), "ivm_ranker_save")
+    buf = ctypes.create_string_buffer(n.value)
+    _check(lib().ivm_ranker_save(ctx.handle, ctypes.cast(buf, _VP), ctypes.byref(n)),
+           "ivm_ranker_save")
+    return buf.raw[:n.value]
+
+
+def ivm_ranker_load(ctx, blob: bytes):
+    buf = ctypes.create_string_buffer(blob, len(blob))
+    _check(lib().ivm_ranker_load(ctx.handle, ctypes.cast(buf, _VP), len(blob)), "ivm_ranker_load")
+
+
+def ivm_ranker_infer(ctx, x):
+    """(logits float32 [B][64], top uint8 [B][8]) from the tensor-core inference kernel."""
+    xx = np.ascontiguousarray(x, dtype=np.float32).reshape(-1, RANKER_IN)
+    logits = np.zeros((xx.shape[0], RANKER_OUT), dtype=np.float32)
+    top = np.zeros((xx.shape[0], 8), dtype=np.uint8)
+    _check(lib().ivm_ranker_infer(ctx.handle, xx.ctypes.data, xx.shape[0], logits.ctypes.data,
+                                  top.ctypes.data), "ivm_ranker_infer")
+    return logits, top
+
+
+def ivm_ranker_gradients(ctx, weights, x, y):
+    """(grads float32 [RANKER_PARAMS], loss) from the GPU training kernels."""
+    w = np.ascontiguousarray(weights, dtype=np.float32)
+    xx = np.ascontiguousarray(x, dtype=np.float32).reshape(-1, RANKER_IN)
+    yy = np.ascontiguousarray(y, dtype=np.int32)
+    g = np.zeros(RANKER_PARAMS, dtype=np.float32)
+    loss = np.zeros(1, dtype=np.float32)
+    _check(lib().ivm_ranker_gradients(ctx.handle, w.ctypes.data, xx.ctypes.data, yy.ctypes.data,
+                                      xx.shape[0], g.ctypes.data, loss.ctypes.data),
+           "ivm_ranker_gradients")
+    return g, float(loss[0])
+
+
 NOALLOC_MAX_FACETS, NOALLOC_MAX_SAMPLES_PER_SIDE = 1024, 5
 
 

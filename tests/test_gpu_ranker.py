@@ -1,0 +1,212 @@
+"""Learned cluster ranker: training and inference kernels against a float64
+CPU reference, training behaviour, and the invariance of every matrix bit
+under the ranker (the learned order only changes which facets are tested
+first, never a verdict)."""
+import struct
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2501_02747_gb300 import ivm
+from paper_2501_02747_gb300 import scenegen as sg
+from tests import ranker_ref
+from tests.gpu_common import to_np
+
+pytestmark = pytest.mark.gpu
+
+FAST = ivm.IVM_FLAG_PERSISTENT | ivm.IVM_FLAG_OCCLUDER_CACHE | ivm.IVM_FLAG_DEDUP_SOURCES
+MAGIC = 0x524D5649
+
+
+def blob_of(w):
+    w = np.ascontiguousarray(w, dtype=np.float32)
+    assert w.size == ivm.RANKER_PARAMS
+    return struct.pack("<6I", MAGIC, 1, 76, 128, 64, ivm.RANKER_PARAMS) + w.tobytes()
+
+
+def weights_of(blob):
+    return np.frombuffer(blob[24:], dtype=np.float32).copy()
+
+
+def he_weights(rng, scale=1.0):
+    parts = []
+    for i, o in ranker_ref.SHAPES:
+        parts.append(rng.uniform(-1, 1, i * o) * np.sqrt(6.0 / i) * scale)
+        parts.append(rng.normal(0, 0.05, o))
+    return np.concatenate(parts)
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import torch
+    from paper_2501_02747_gb300 import build
+    build.build()
+    c = ivm.Context(0, torch.cuda.current_stream(0))
+    yield c
+    c.close()
+
+
+@pytest.fixture()
+def fresh_ctx():
+    import torch
+    c = ivm.Context(0, torch.cuda.current_stream(0))
+    yield c
+    c.close()
+
+
+@pytest.mark.parametrize("batch", [1, 7, 512, 777])
+def test_gradients_match_float64_reference(ctx, batch):
+    rng = np.random.default_rng(100 + batch)
+    w = he_weights(rng).astype(np.float32)
+    x = rng.random((batch, 76)).astype(np.float32)
+    y = rng.integers(0, 64, batch).astype(np.int32)
+    g, loss = ivm.ivm_ranker_gradients(ctx, w, x, y)
+    want_loss, want_g = ranker_ref.loss_and_grad(w.astype(np.float64), x.astype(np.float64), y)
+    assert abs(loss - want_loss) <= 1e-4 * max(1.0, abs(want_loss))
+    # FP32 sums of at most ~800 terms: relative to the block's largest entry
+    off = 0
+    for i, o in ranker_ref.SHAPES:
+        for n in (i * o, o):
+            a, b = g[off:off + n], want_g[off:off + n]
+            scale = max(np.abs(b).max(), 1e-12)
+            assert np.abs(a - b).max() <= 2e-4 * scale, (off, np.abs(a - b).max(), scale)
+            off += n
+
+
+def test_gradients_reject_bad_labels(ctx):
+    w = np.zeros(ivm.RANKER_PARAMS, np.float32)
+    x = np.zeros((2, 76), np.float32)
+    with pytest.raises(ivm.IvmError):
+        ivm.ivm_ranker_gradients(ctx, w, x, np.array([0, 64], np.int32))
+
+
+def test_inference_kernel_matches_float64_reference(fresh_ctx):
+    rng = np.random.default_rng(7)
+    w = he_weights(rng)
+    ivm.ivm_ranker_load(fresh_ctx, blob_of(w))
+    x = rng.random((1000, 76)).astype(np.float32)     # ragged: 1000 = 62 tiles of 16 + 8
+    logits, top = ivm.ivm_ranker_infer(fresh_ctx, x)
+    # float64 forward of the same weights
+    h = x.astype(np.float64)
+    for k, (W, b) in enumerate(ranker_ref.unpack(w.astype(np.float32).astype(np.float64))):
+        h = h @ W + b
+        if k < 3:
+            h = np.maximum(h, 0)
+    # BF16 operands (8-bit mantissa) through four layers: a few per cent of the logit scale
+    scale = np.abs(h).max()
+    assert np.abs(logits - h).max() <= 0.05 * scale, (np.abs(logits - h).max(), scale)
+    # the packed top 8 is exactly the top 8 of the kernel's own logits (ties to the lower index)
+    order = np.lexsort((np.tile(np.arange(64), (len(x), 1)), -logits), axis=1)[:, :8]
+    assert (top == order).all()
+    # and the float64 winner is among the kernel's first proposals
+    best = h.argmax(axis=1)
+    assert np.mean([best[i] in top[i, :3] for i in range(len(x))]) > 0.95
+
+
+def test_infer_requires_a_ranker(fresh_ctx):
+    with pytest.raises(ivm.IvmError):
+        ivm.ivm_ranker_infer(fresh_ctx, np.zeros((1, 76), np.float32))
+
+
+def test_load_rejects_bad_blobs(fresh_ctx):
+    b = blob_of(np.zeros(ivm.RANKER_PARAMS))
+    for bad in (b[:-4], b"XXXX" + b[4:], b[:8] + struct.pack("<I", 77) + b[12:]):
+        with pytest.raises(ivm.IvmError):
+            ivm.ivm_ranker_load(fresh_ctx, bad)
+    with pytest.raises(ivm.IvmError):
+        ivm.ivm_ranker_save(fresh_ctx)          # nothing trained or loaded
+
+
+@pytest.fixture(scope="module")
+def trained(ctx):
+    """Ranker trained on the degenerate district (10 buildings of zero height
+    or width among 1,001 facets) and the tiny scene."""
+    tiny, deg = sg.tiny(), sg.degenerate(n_snap=16)
+    first = ivm.ivm_ranker_train(ctx, [tiny.facets, deg.facets], 5, epochs=1, lr=2e-3)
+    last = ivm.ivm_ranker_train(ctx, [tiny.facets, deg.facets], 5, epochs=12, lr=2e-3)
+    return first, last, ivm.ivm_ranker_save(ctx)
+
+
+def test_training_lowers_the_loss(trained):
+    first, last, _ = trained
+    assert first < np.log(64)
+    assert last < first
+    assert np.isfinite(last)
+
+
+def test_save_load_round_trip(trained, fresh_ctx):
+    _, _, blob = trained
+    ivm.ivm_ranker_load(fresh_ctx, blob)
+    assert ivm.ivm_ranker_save(fresh_ctx) == blob
+    assert np.isfinite(weights_of(blob)).all()
+
+
+def test_training_is_deterministic(trained, fresh_ctx):
+    """Fixed initial weights, shuffle and batch order: the same weights again."""
+    _, last, blob = trained
+    tiny, deg = sg.tiny(), sg.degenerate(n_snap=16)
+    ivm.ivm_ranker_train(fresh_ctx, [tiny.facets, deg.facets], 5, epochs=12, lr=2e-3)
+    w1, w2 = weights_of(blob), weights_of(ivm.ivm_ranker_save(fresh_ctx))
+    assert np.abs(w1 - w2).max() <= 1e-3 * max(1.0, np.abs(w1).max())
+
+
+@pytest.mark.parametrize("flags", [0, ivm.IVM_FLAG_PERSISTENT, FAST, FAST | ivm.IVM_FLAG_GRAPH])
+def test_learned_matrix_equals_oracle(trained, fresh_ctx, flags):
+    _, _, blob = trained
+    ivm.ivm_ranker_load(fresh_ctx, blob)
+    sc = sg.tiny()
+    M, st = ivm.ivm_build_matrix(fresh_ctx, sc.facets, 3, mode=ivm.IVM_MODE_LEARNED, flags=flags)
+    assert (to_np(M) == oracle.matrix(sc.facets, 3)).all()
+    for seed in (11, 12):
+        sm = sg.random_small_city(seed, n_buildings=6, n_snap=4, s=2)
+        M, _ = ivm.ivm_build_matrix(fresh_ctx, sm.facets, 2, mode=ivm.IVM_MODE_LEARNED, flags=flags)
+        assert (to_np(M) == oracle.matrix(sm.facets, 2)).all()
+
+
+def test_learned_matrix_independent_of_weights(trained, fresh_ctx):
+    """Trained, random, all-zero (every logit tied) and absent rankers: one matrix."""
+    _, _, blob = trained
+    sc = sg.degenerate(n_snap=16)
+    want, _ = ivm.ivm_build_matrix(fresh_ctx, sc.facets, 5, mode=ivm.IVM_MODE_FILTERED, flags=FAST)
+    want = to_np(want)
+    got0, st0 = ivm.ivm_build_matrix(fresh_ctx, sc.facets, 5, mode=ivm.IVM_MODE_LEARNED, flags=FAST)
+    assert (to_np(got0) == want).all()
+    assert st0.ranker_hits == 0
+    rng = np.random.default_rng(3)
+    for b in (blob, blob_of(he_weights(rng, 3.0)), blob_of(np.zeros(ivm.RANKER_PARAMS))):
+        ivm.ivm_ranker_load(fresh_ctx, b)
+        for flags in (0, FAST):
+            got, _ = ivm.ivm_build_matrix(fresh_ctx, sc.facets, 5, mode=ivm.IVM_MODE_LEARNED,
+                                          flags=flags)
+            assert (to_np(got) == want).all()
+    rows = np.random.default_rng(5).choice(sc.facets.shape[0], 24, replace=False)
+    assert (want[rows] == oracle.matrix(sc.facets, 5, rows=rows)).all()
+
+
+def test_learned_batched_scenes(trained, fresh_ctx):
+    _, _, blob = trained
+    ivm.ivm_ranker_load(fresh_ctx, blob)
+    scenes = [sg.random_small_city(20 + k, n_buildings=3 + k, n_snap=2, s=2).facets for k in range(4)]
+    Ms, _ = ivm.ivm_build_matrix(fresh_ctx, scenes, 2, mode=ivm.IVM_MODE_LEARNED, flags=FAST)
+    for F, M in zip(scenes, Ms):
+        assert (to_np(M) == oracle.matrix(F, 2)).all()
+
+
+def test_ranker_gain_is_reported(trained, fresh_ctx):
+    """Work per blocked-candidate segment with and without the trained ranker
+    on the district (printed; the verdicts are identical either way)."""
+    _, _, blob = trained
+    sc = sg.district(n_snap=16)
+    Mf, sf = ivm.ivm_build_matrix(fresh_ctx, sc.facets, 5, mode=ivm.IVM_MODE_FILTERED,
+                                  flags=ivm.IVM_FLAG_PERSISTENT)
+    ivm.ivm_ranker_load(fresh_ctx, blob)
+    Ml, sl = ivm.ivm_build_matrix(fresh_ctx, sc.facets, 5, mode=ivm.IVM_MODE_LEARNED,
+                                  flags=ivm.IVM_FLAG_PERSISTENT)
+    assert (to_np(Mf) == to_np(Ml)).all()
+    assert sl.segments == sf.segments and sl.cand_pairs == sf.cand_pairs
+    assert sl.ranker_hits > 0
+    print(f"\nfiltered: node {sf.node_tests / sf.segments:.2f} leaf {sf.leaf_tests / sf.segments:.2f}"
+          f" per segment, {sf.ms_traverse:.3f} ms; learned: node {sl.node_tests / sl.segments:.2f}"
+          f" leaf {sl.leaf_tests / sl.segments:.2f}, {sl.ms_traverse:.3f} ms,"
+          f" first-proposal hits {sl.ranker_hits}")

@@ -174,7 +174,7 @@ def run_reference(args, ws, rank):
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int128",
+        "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "int128",
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "oracle": "brute force, every segment against every "
                    "triangle, exact int128 (oracle/ivm_oracle.c)"},
@@ -209,7 +209,7 @@ def run_ours(args, ws, rank, local):
     import numpy as np
     import torch
 
-    from paper_2501_02747_gb300 import build, ivm
+    from paper_2501_02747_gb300 import build, ivm, shard
     from paper_2501_02747_gb300 import scenegen as sg
     build.build()
     torch.cuda.set_device(local)
@@ -218,7 +218,9 @@ def run_ours(args, ws, rank, local):
     sc = sg.district()
     N, S, K, s = sc.n_facets, sc.n_snap, sc.max_order, sc.samples_per_side
     W = ivm.words(N)
-    units = N * N + 2 * N * S
+    units = N * N + 2 * N * S   # the whole job's units (split across ranks when ws > 1)
+    rows = shard.row_ranges(N, ws)[rank]
+    snap_a, snap_b = shard.snapshot_ranges(S, ws)[rank]
     ctx = ivm.Context(local, stream)
     facets_d = torch.from_numpy(sc.facets).to(dev)
     tx_d = torch.from_numpy(sc.tx).to(dev)
@@ -253,18 +255,26 @@ def run_ours(args, ws, rank, local):
     train_s = time.perf_counter() - t0
 
     def step(form, fac, tx, rx, M, T, L, summ, marks=None):
-        """The three calls; `marks` (4 CUDA events) bracket them on the stream."""
+        """The three calls; `marks` (4 CUDA events) bracket them on the stream.
+        With ws > 1 this rank's share: its matrix rows, the all-reduce of the
+        parts, then the table and tree of its snapshot range."""
         kw = forms[form]
         kw_m, kw_t = shape[form]
         if marks:
             marks[0].record(stream)
-        _, stm = ivm.ivm_build_matrix(ctx, fac, s, out=M, **kw, **kw_m)
+        if ws == 1:
+            _, stm = ivm.ivm_build_matrix(ctx, fac, s, out=M, **kw, **kw_m)
+        else:
+            _, stm = ivm.ivm_build_matrix_rows(ctx, fac, s, rows, out=M, **kw, **kw_m)
+            shard.exchange_matrix(M)
         if marks:
             marks[1].record(stream)
-        _, stt = ivm.ivm_build_table(ctx, fac, s, tx, rx, out=(T, L), **kw, **kw_t)
+        a, b = snap_a, snap_b
+        _, stt = ivm.ivm_build_table(ctx, fac, s, tx[a:b], rx[a:b], out=(T[a:b], L[a:b]),
+                                     **kw, **kw_t)
         if marks:
             marks[2].record(stream)
-        ivm.ivm_expand_image_tree(ctx, M, T, L, N, K, summary=summ)
+        ivm.ivm_expand_image_tree(ctx, M, T[a:b], L[a:b], N, K, summary=summ[a:b])
         if marks:
             marks[3].record(stream)
         return stm, stt
@@ -341,26 +351,29 @@ def run_ours(args, ws, rank, local):
     def per_seg(st, key):
         return st[key] / st["segments"] if st["segments"] else None
 
-    value = ws * units / (ms_fast / 1e3)
+    value = units / (ms_fast / 1e3)
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_fast, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "int64/int128 + fp32 filter",
+        "scaling": "strong", "vs_baseline": None, "dtype": "int64/int128 + fp32 filter",
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "form": "fast: FP32 filter + exact fallback, "
                    "persistent work queue, occluder cache, one row per run of equal "
                    "source positions, CUDA-graph replay of each call",
                    "l2": "flushed between steps (512 MB write)",
                    "facets": N, "snapshots": S, "samples_per_side": s, "max_order": K,
-                   "pair_tests_per_step": units, "autotuned_shape": tuned},
-        "snapshot_tables_per_s": ws * S / (ms_fast / 1e3),
-        "plain": {"ms_per_step": ms_plain, "value": ws * units / (ms_plain / 1e3),
+                   "pair_tests_per_step": units, "autotuned_shape": tuned,
+                   "parallelism": "one workload split over ranks: matrix rows of about equal "
+                                  "pair counts, one all-reduce of the matrix parts, snapshot "
+                                  "ranges for the table and tree" if ws > 1 else "1 GPU"},
+        "snapshot_tables_per_s": S / (ms_fast / 1e3),
+        "plain": {"ms_per_step": ms_plain, "value": units / (ms_plain / 1e3),
                   "form": "exact int64/int128 facet tests, one warp per work item"},
         "speedup_vs_plain": ms_plain / ms_fast,
         "learned": {
             "form": "fast + learned cluster order in the matrix call (BF16 MLP ranking of "
                     "64 BVH subtrees per candidate pair, tensor-core inference)",
-            "ms_per_step": ms_lrn, "value": ws * units / (ms_lrn / 1e3),
+            "ms_per_step": ms_lrn, "value": units / (ms_lrn / 1e3),
             "speedup_vs_plain": ms_plain / ms_lrn,
             "matrix_ms_per_call": calls_lrn["matrix"],
             "matrix_ms_per_call_without_ranker": calls_fast["matrix"],
@@ -404,21 +417,43 @@ def run_ours(args, ws, rank, local):
         T_h = torch.empty((S, 2, W), dtype=torch.int32).pin_memory()
         L_h = torch.empty((S,), dtype=torch.uint8).pin_memory()
         summ_h = torch.empty((S, K + 1, 3), dtype=torch.int64).pin_memory()
+        a, b = snap_a, snap_b
+
+        def e2e_step():
+            if ws == 1:   # the library copies host buffers in and out itself
+                step("fast", fac_h, tx_h, rx_h, M_h, T_h, L_h, summ_h)
+                return
+            # the all-reduce needs device buffers: stage this rank's inputs and outputs
+            facets_d.copy_(fac_h, non_blocking=True)
+            tx_d[a:b].copy_(tx_h[a:b], non_blocking=True)
+            rx_d[a:b].copy_(rx_h[a:b], non_blocking=True)
+            step("fast", facets_d, tx_d, rx_d, M_d, T_d, L_d, summ_d)
+            M_h.copy_(M_d)
+            T_h[a:b].copy_(T_d[a:b])
+            L_h[a:b].copy_(L_d[a:b])
+            summ_h[a:b].copy_(summ_d[a:b])
+
         for _ in range(max(1, args.warmup)):
-            step("fast", fac_h, tx_h, rx_h, M_h, T_h, L_h, summ_h)
+            e2e_step()
         torch.cuda.synchronize()
         barrier(ws)
         t0 = time.perf_counter()
         for _ in range(args.steps):
-            step("fast", fac_h, tx_h, rx_h, M_h, T_h, L_h, summ_h)
+            e2e_step()
         torch.cuda.synchronize()
         e2e_s = max_over_ranks(ws, time.perf_counter() - t0) / args.steps
-        h2d = 2 * fac_h.numel() * 4 + tx_h.numel() * 4 + rx_h.numel() * 4 + \
-            M_h.numel() * 4 + T_h.numel() * 4 + L_h.numel()
-        d2h = M_h.numel() * 4 + T_h.numel() * 4 + L_h.numel() + summ_h.numel() * 8
-        out["e2e"] = {"value": ws * units / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
+        Sr = b - a
+        if ws == 1:   # facets go in for both calls; the matrix goes out and back in
+            h2d = 2 * fac_h.numel() * 4 + 2 * Sr * 3 * 4 + M_h.numel() * 4 + \
+                Sr * 2 * W * 4 + Sr
+        else:
+            h2d = fac_h.numel() * 4 + 2 * Sr * 3 * 4
+        d2h = M_h.numel() * 4 + Sr * 2 * W * 4 + Sr + Sr * (K + 1) * 3 * 8
+        out["e2e"] = {"value": units / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
                       "d2h_bytes_per_step": d2h, "ms_per_step": 1e3 * e2e_s,
-                      "path": "same three C-ABI calls with pinned host buffers"}
+                      "path": "same C-ABI calls with pinned host buffers" + (
+                          "" if ws == 1 else ", staged through device buffers for the "
+                          "all-reduce (rank 0's bytes)")}
 
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         threads = os.cpu_count() or 1

@@ -138,6 +138,18 @@ int ivm_destroy(ivm_ctx *ctx);
 int ivm_build_matrix(ivm_ctx *ctx, const ivm_scene *scenes, int32_t n_scenes,
                      const ivm_params *params, uint32_t *const *matrix, ivm_stats *stats);
 
+/* One part of the matrix, for splitting the work across devices (rows are
+ * independent given the scene).  Decides only the unordered pairs (i, j),
+ * i < j, with row_begin[k] <= i < row_end[k], and writes both of their bits
+ * (row i and row j); every other bit of matrix[k] is 0.  Over a partition of
+ * [0, N_k) into row ranges, the bitwise OR -- or, the bit sets being
+ * disjoint, the integer sum -- of the parts is the ivm_build_matrix result.
+ * stats->pairs counts the ordered pairs the part decides.  Errors: as
+ * ivm_build_matrix; IVM_ERR_ARG if a range is not 0 <= begin <= end <= N_k. */
+int ivm_build_matrix_rows(ivm_ctx *ctx, const ivm_scene *scenes, int32_t n_scenes,
+                          const ivm_params *params, const int32_t *row_begin,
+                          const int32_t *row_end, uint32_t *const *matrix, ivm_stats *stats);
+
 /* Inter-visibility table for specific points along the route (Sec. III-B/C,
  * Table II).  For scene k: tx[k], rx[k] are [n_snap[k]][3] int32 cm;
  * table[k] receives [n_snap[k]][2][W_k] words (row 0 the Tx's visible

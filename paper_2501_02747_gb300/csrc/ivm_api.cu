@@ -180,6 +180,8 @@ int plan_geometry(ivm_ctx *c, const ivm_scene *scenes, int n_scenes, int s, DevS
         D.s = s;
         D.sample0 = (int)samples;
         D.rw0 = rw;
+        D.row_lo = 0;
+        D.row_hi = S.n_facets;
         facets += S.n_facets;
         nodes += S.n_facets - 1;
         samples += (long long)S.n_facets * s * s;
@@ -473,11 +475,13 @@ extern "C" int ivm_destroy(ivm_ctx *c)
     return IVM_OK;
 }
 
-extern "C" int ivm_build_matrix(ivm_ctx *c, const ivm_scene *scenes, int32_t n_scenes,
-                                const ivm_params *params, uint32_t *const *matrix,
-                                ivm_stats *stats)
+namespace {
+
+int build_matrix(ivm_ctx *c, const ivm_scene *scenes, int32_t n_scenes, const ivm_params *params,
+                 const int32_t *row_begin, const int32_t *row_end, uint32_t *const *matrix,
+                 ivm_stats *stats)
 {
-    if (!c || !matrix) return IVM_ERR_ARG;
+    if (!c || !matrix || (!row_begin != !row_end)) return IVM_ERR_ARG;
     int r = check_params(params);
     if (r) return r;
     DeviceGuard dg(c->device);
@@ -492,11 +496,21 @@ extern "C" int ivm_build_matrix(ivm_ctx *c, const ivm_scene *scenes, int32_t n_s
     unsigned long long pairs_total = 0;
     for (int k = 0; k < n_scenes; k++) {
         if (!matrix[k]) return IVM_ERR_ARG;
+        const long long n = hd[k].n;
+        if (row_begin) {
+            if (row_begin[k] < 0 || row_begin[k] > row_end[k] || row_end[k] > n) return IVM_ERR_ARG;
+            hd[k].row_lo = row_begin[k];
+            hd[k].row_hi = row_end[k];
+        }
         on_host[k] = !is_device(matrix[k]);
         all_device &= !on_host[k] && is_device(scenes[k].facets);
         if (on_host[k]) host_words += (size_t)hd[k].n * hd[k].W;
-        upper += (long long)hd[k].n * (hd[k].n - 1) / 2;
-        pairs_total += (unsigned long long)hd[k].n * hd[k].n;
+        // unordered pairs (i < j) with row_lo <= i < row_hi, and the ordered
+        // pairs they decide (both bits, plus the diagonal of those rows)
+        const long long lo = hd[k].row_lo, hi = hd[k].row_hi;
+        const long long part = (hi - lo) * (n - 1) - (lo + hi - 1) * (hi - lo) / 2;
+        upper += part;
+        pairs_total += (unsigned long long)(2 * part + (hi - lo));
     }
     const LaunchCfg cfg0 = launch_cfg(c, params);
     const bool dev_count = cfg0.persistent && upper <= kDevCountMaxPairs;
@@ -564,6 +578,8 @@ extern "C" int ivm_build_matrix(ivm_ctx *c, const ivm_scene *scenes, int32_t n_s
             key.push_back((unsigned long long)(uintptr_t)scenes[k].facets);
             key.push_back((unsigned long long)scenes[k].n_facets);
             key.push_back((unsigned long long)(uintptr_t)matrix[k]);
+            key.push_back(((unsigned long long)(unsigned)hd[k].row_lo << 32) |
+                          (unsigned)hd[k].row_hi);
         }
         GraphEntry *ge = find_graph(c, key);
         if (!ge && (r = capture_graph(c, key, sizeof(SceneDesc) * n_scenes, hd.data(), enqueue,
@@ -581,6 +597,24 @@ extern "C" int ivm_build_matrix(ivm_ctx *c, const ivm_scene *scenes, int32_t n_s
                                cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     return fill_stats(c, stats, pairs_total, 3);
+}
+
+}  // namespace
+
+extern "C" int ivm_build_matrix(ivm_ctx *c, const ivm_scene *scenes, int32_t n_scenes,
+                                const ivm_params *params, uint32_t *const *matrix,
+                                ivm_stats *stats)
+{
+    return build_matrix(c, scenes, n_scenes, params, nullptr, nullptr, matrix, stats);
+}
+
+extern "C" int ivm_build_matrix_rows(ivm_ctx *c, const ivm_scene *scenes, int32_t n_scenes,
+                                     const ivm_params *params, const int32_t *row_begin,
+                                     const int32_t *row_end, uint32_t *const *matrix,
+                                     ivm_stats *stats)
+{
+    if (!row_begin || !row_end) return IVM_ERR_ARG;
+    return build_matrix(c, scenes, n_scenes, params, row_begin, row_end, matrix, stats);
 }
 
 extern "C" int ivm_build_table(ivm_ctx *c, const ivm_scene *scenes, int32_t n_scenes,

@@ -59,6 +59,8 @@ struct SceneDesc {
     uint8_t *los;     // [S]
     long long snap0;  // first index of this scene in the global snapshot space
     long long nsnap;
+    int row_lo;       // matrix: only pairs (i, j), i < j, with row_lo <= i < row_hi
+    int row_hi;
 };
 
 // Device counters (u64), summed into ivm_stats.

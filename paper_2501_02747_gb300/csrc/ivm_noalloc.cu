@@ -122,6 +122,8 @@ extern "C" int ivm_build_matrix_noalloc(const ivm_facet *facets, int32_t n_facet
     hd.sample0 = 0;
     hd.rw0 = 0;
     hd.matrix = matrix;
+    hd.row_lo = 0;
+    hd.row_hi = n_facets;
 
     DevScenes g = {};
     g.n_scenes = 1;

@@ -44,6 +44,7 @@ __device__ __forceinline__ bool screen_lane(const DevScenes &g, long long w, int
     i = (int)(local / D.W);
     int c = (int)(local - (long long)i * D.W);
     j = 32 * c + (threadIdx.x & 31);
+    if (i < D.row_lo || i >= D.row_hi) return false;   // another part's rows (warp-uniform)
     if (j <= i || j >= D.n) return false;
     const Leaf Li = load_leaf(g.leaf, D.facet0 + i);
     const Leaf Lj = load_leaf(g.leaf, D.facet0 + j);

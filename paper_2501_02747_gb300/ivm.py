@@ -65,6 +65,10 @@ SIGNATURES = {
     "ivm_build_matrix": ([_VP, ctypes.POINTER(ivm_scene), ctypes.c_int32,
                           ctypes.POINTER(ivm_params), ctypes.POINTER(_VP),
                           ctypes.POINTER(ivm_stats)], ctypes.c_int),
+    "ivm_build_matrix_rows": ([_VP, ctypes.POINTER(ivm_scene), ctypes.c_int32,
+                               ctypes.POINTER(ivm_params), ctypes.POINTER(ctypes.c_int32),
+                               ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(_VP),
+                               ctypes.POINTER(ivm_stats)], ctypes.c_int),
     "ivm_build_table": ([_VP, ctypes.POINTER(ivm_scene), ctypes.c_int32,
                          ctypes.POINTER(ivm_params), ctypes.POINTER(_VP), ctypes.POINTER(_VP),
                          ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(_VP),
@@ -306,6 +310,35 @@ def ivm_build_matrix(ctx, facets, s, mode=IVM_MODE_EXACT, flags=0, tile=0, warps
     p = _params(s, 0, mode, tile, warps_per_block, flags)
     _check(lib().ivm_build_matrix(ctx.handle, scenes, len(flist), ctypes.byref(p), ptrs,
                                   ctypes.byref(st)), "ivm_build_matrix")
+    return (out[0] if single else out), st
+
+
+def ivm_build_matrix_rows(ctx, facets, s, rows, mode=IVM_MODE_EXACT, flags=0, tile=0,
+                          warps_per_block=0, out=None):
+    """The part of the matrix decided by the pairs (i < j) whose row i lies in
+    `rows` = (begin, end) (one scene) or a list of ranges (one per scene).
+
+    Returns the part (bits of other pairs 0) and an ivm_stats, like
+    ivm_build_matrix; the sum over a partition of the rows is the matrix."""
+    import torch
+    single = not isinstance(facets, (list, tuple))
+    flist = [facets] if single else list(facets)
+    rlist = [rows] if single else list(rows)
+    if len(rlist) != len(flist):
+        raise ValueError("one row range per scene")
+    scenes, keep = _scenes(flist)
+    if out is None:
+        out = [torch.empty((f.shape[0], words(f.shape[0])), dtype=torch.int32,
+                           device=f"cuda:{ctx.device}") for f in flist]
+    elif single:
+        out = [out]
+    ptrs = (_VP * len(out))(*[_addr(o) for o in out])
+    begin = (ctypes.c_int32 * len(flist))(*[int(r[0]) for r in rlist])
+    end = (ctypes.c_int32 * len(flist))(*[int(r[1]) for r in rlist])
+    st = ivm_stats()
+    p = _params(s, 0, mode, tile, warps_per_block, flags)
+    _check(lib().ivm_build_matrix_rows(ctx.handle, scenes, len(flist), ctypes.byref(p), begin,
+                                       end, ptrs, ctypes.byref(st)), "ivm_build_matrix_rows")
     return (out[0] if single else out), st
 
 

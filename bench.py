@@ -52,8 +52,8 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     # profiling case: one phase of one form on the first N snapshots (no JSON contract line)
-    p.add_argument("--profile", choices=["matrix", "table", "tree"], default=None)
-    p.add_argument("--form", choices=["fast", "plain"], default="fast")
+    p.add_argument("--profile", choices=["matrix", "table", "tree", "step"], default=None)
+    p.add_argument("--form", choices=["fast", "plain", "learned"], default="fast")
     p.add_argument("--snapshots", type=int, default=None)
     return p.parse_args()
 
@@ -280,22 +280,33 @@ def run_ours(args, ws, rank, local):
         return stm, stt
 
     if args.profile:
-        # small profiling case: one phase, first --snapshots snapshots
+        # profiling case: one phase of one form (launch shape as timed), on the
+        # first --snapshots snapshots; the calls after the warm-up run inside
+        # the NVTX range "profile_<phase>" (ncu --nvtx --nvtx-include)
         Sp = min(S, args.snapshots or S)
         kw = forms[args.form]
-        for _ in range(args.warmup + args.steps):
-            if args.profile == "matrix":
-                _, st = ivm.ivm_build_matrix(ctx, facets_d, s, out=M_d, **kw)
-            elif args.profile == "table":
+        kw_m, kw_t = shape[args.form]
+        st = None
+        for it in range(args.warmup + args.steps):
+            if it == args.warmup:
+                torch.cuda.synchronize()
+                torch.cuda.nvtx.range_push(f"profile_{args.profile}")
+            if args.profile in ("matrix", "step"):
+                _, st = ivm.ivm_build_matrix(ctx, facets_d, s, out=M_d, **kw, **kw_m)
+            if args.profile in ("table", "step"):
                 _, st = ivm.ivm_build_table(ctx, facets_d, s, tx_d[:Sp], rx_d[:Sp],
-                                            out=(T_d[:Sp], L_d[:Sp]), **kw)
-            else:
-                ivm.ivm_build_matrix(ctx, facets_d, s, out=M_d, **kw)
-                ivm.ivm_build_table(ctx, facets_d, s, tx_d[:Sp], rx_d[:Sp],
-                                    out=(T_d[:Sp], L_d[:Sp]), **kw)
+                                            out=(T_d[:Sp], L_d[:Sp]), **kw, **kw_t)
+            if args.profile in ("tree", "step"):
+                if args.profile == "tree" and it == 0:
+                    ivm.ivm_build_matrix(ctx, facets_d, s, out=M_d, **kw, **kw_m)
+                    ivm.ivm_build_table(ctx, facets_d, s, tx_d[:Sp], rx_d[:Sp],
+                                        out=(T_d[:Sp], L_d[:Sp]), **kw, **kw_t)
                 ivm.ivm_expand_image_tree(ctx, M_d, T_d[:Sp], L_d[:Sp], N, K, summary=summ_d[:Sp])
-                st = None
         torch.cuda.synchronize()
+        if args.steps:
+            torch.cuda.nvtx.range_pop()
+        if args.profile == "step":
+            st = None
         print(json.dumps({"profile": args.profile, "form": args.form, "snapshots": Sp,
                           "stats": st.as_dict() if st is not None else None}))
         ctx.close()
@@ -312,6 +323,7 @@ def run_ours(args, ws, rank, local):
         ops, node_tests, leaf_tests = {"matrix": 0, "table": 0}, 0, 0
         calls = {"matrix": 0.0, "table": 0.0, "tree": 0.0}
         stats = None
+        torch.cuda.nvtx.range_push(f"timed_{form}")
         for _ in range(args.steps):
             flush.zero_()
             ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
@@ -327,6 +339,7 @@ def run_ours(args, ws, rank, local):
                 ops[name] += st.node_tests * FP32_OPS_PER_NODE_TEST + \
                     leaf_fp * FP32_OPS_PER_FILTERED_LEAF
             stats = (stm.as_dict(), stt.as_dict())
+        torch.cuda.nvtx.range_pop()
         launches = ivm.kernel_launches() - launches0
         torch.cuda.synchronize()
         barrier(ws)

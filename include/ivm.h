@@ -96,7 +96,7 @@ typedef struct ivm_params {
     int32_t tile;             /* matrix: candidate pairs per queue pop (0 = default) */
     int32_t warps_per_block;  /* 1..4 (0 = default 4) */
     int32_t flags;            /* IVM_FLAG_* */
-    int32_t table_tile;       /* table: consecutive snapshots per work item (0 = 16) */
+    int32_t table_tile;       /* table: consecutive snapshots per work item (0 = 32) */
 } ivm_params;
 
 typedef struct ivm_stats {

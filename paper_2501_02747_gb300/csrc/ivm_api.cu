@@ -631,7 +631,7 @@ extern "C" int ivm_build_table(ivm_ctx *c, const ivm_scene *scenes, int32_t n_sc
     // ---- plan
     if ((r = plan_geometry(c, scenes, n_scenes, params->samples_per_side, g, hd))) return r;
     long long snaps = 0, chunks = 0, items = 0;
-    const int snap_tile = params->table_tile > 0 ? params->table_tile : 16;
+    const int snap_tile = params->table_tile > 0 ? params->table_tile : 32;
     size_t host_tab = 0, host_los = 0, pos_tx = 0, pos_rx = 0;
     std::vector<char> tab_host(n_scenes), los_host(n_scenes), tx_host(n_scenes),
         rx_host(n_scenes);
@@ -1180,7 +1180,7 @@ extern "C" int ivm_autotune(ivm_ctx *c, const ivm_scene *scenes, int32_t n_scene
     base.flags &= ~IVM_FLAG_GRAPH;
     const int wpbs[] = {2, 4};
     const int mtiles[] = {1, 2, 4, 8, 16};
-    const int ttiles[] = {4, 8, 16, 32, 64};
+    const int ttiles[] = {8, 16, 32, 64, 128, 256};
     float best_total = 1e30f;
     ivm_params best = *params;
     for (int wpb : wpbs) {

@@ -23,6 +23,16 @@
 // Runs of equal positions (a static Tx, a receiver that pauses) have equal
 // rows: with deduplication on, a pre-pass finds the first snapshot of each
 // run, only that row is traced, and a post-pass copies it over the run.
+//
+// Hidden facets are settled for a whole tile at once when the tile's
+// positions lie on the segment between its first and last position (a
+// straight stretch of route).  For a convex facet F and a sample q, the
+// positions a from which the open segment a-q meets F form the convex set
+// {q + L (f - q) : f in F, L > 1}; so if F blocks every sample segment of
+// facet j from both end positions, it blocks them from every position of
+// the tile, and j is hidden at all of the tile's snapshots.  F is the facet
+// that hid j at the tile's first traced snapshot; the two end tests per
+// sample are the same exact facet tests as everywhere else.
 #include "ivm_internal.cuh"
 #include "traverse.cuh"
 #include "filter.cuh"
@@ -33,6 +43,13 @@ namespace ivm {
 // warp's recently used occluders before a walk.
 constexpr bool kTableProbe = true;
 constexpr bool kTableLru = true;
+constexpr bool kTableTileProof = true;
+constexpr bool kTableBatchProbe = true;
+// Per-sample temporal blockers (shared memory, 32 facets x 32 samples per warp).
+constexpr bool kTableSampleBlockers = true;
+constexpr int kSampleSlots = 32 * 32;
+// Snapshots per straight-stretch proof (a work item may hold several).
+constexpr int kProofTile = 32;
 
 __device__ __forceinline__ int scene_of_snap(const SceneDesc *desc, int n_scenes, long long T)
 {
@@ -125,10 +142,105 @@ __device__ __forceinline__ unsigned table_packet(const DevScenes &g, const Scene
                                   err, wc, leaf, cache, myblk);
 }
 
+// Facets of word c (lanes with blk >= 0 hold a candidate blocker) that the
+// blocker hides from both a = (ax, ay, az) and e = (ex, ey, ez), at every
+// sample: their bits are set in the returned (warp-uniform) mask.
+template <class LeafFn>
+__device__ __noinline__ unsigned tile_hidden(const DevScenes &g, const SceneDesc &D, int c,
+                                             int blk, const int *pa, const int *pe, int k,
+                                             const int *sblk, WalkCounters &wc, LeafFn leaf)
+{
+    const int lane = threadIdx.x & 31;
+    const int s2 = D.s * D.s;
+    const int ax = k * pa[0], ay = k * pa[1], az = k * pa[2];   // in range: checked
+    const int ex = k * pe[0], ey = k * pe[1], ez = k * pe[2];
+    unsigned cm = __ballot_sync(kFull, blk >= 0);
+    unsigned hidden = 0;
+    while (cm) {
+        if (s2 <= 32) {   // floor(32 / s2) facets per packet, lane = sample
+            const int G = 32 / s2;
+            const int cnt = min(G, __popc(cm));
+            const int gi = lane / s2, b = lane - gi * s2;
+            const bool mine = gi < cnt;
+            unsigned m = cm;
+            for (int q = 0; q < gi && q < 31; q++) m &= m - 1;
+            const int jbit = mine ? __ffs(m) - 1 : 0;
+            int tb = __shfl_sync(kFull, blk, jbit);
+            if (sblk && mine && sblk[32 * jbit + b] >= 0) tb = sblk[32 * jbit + b];
+            bool hit = true;
+            if (mine) {
+                const int si = D.sample0 + (32 * c + jbit) * s2 + b;
+                const int qx = __ldg(g.sx + si), qy = __ldg(g.sy + si), qz = __ldg(g.sz + si);
+                const Leaf F = load_leaf(g.leaf, tb);
+                wc.leaf_tests += 2;
+                hit = leaf(make_seg(ax, ay, az, qx, qy, qz), F, wc) &&
+                      leaf(make_seg(ex, ey, ez, qx, qy, qz), F, wc);
+            }
+            const unsigned hm = __ballot_sync(kFull, hit);
+            const unsigned smask = (s2 == 32) ? kFull : ((1u << s2) - 1u);
+            const bool all = mine && ((hm >> (gi * s2)) & smask) == smask;
+            hidden |= __reduce_or_sync(kFull, (all && b == 0) ? (1u << jbit) : 0u);
+            for (int q = 0; q < cnt; q++) cm &= cm - 1;
+        } else {          // one facet, 32 samples at a time
+            const int jbit = __ffs(cm) - 1;
+            cm &= cm - 1;
+            const int tb = __shfl_sync(kFull, blk, jbit);
+            const Leaf F = load_leaf(g.leaf, tb);
+            bool all = true;
+            for (int b0 = 0; b0 < s2 && all; b0 += 32) {
+                const int b = b0 + lane;
+                bool hit = true;
+                if (b < s2) {
+                    const int si = D.sample0 + (32 * c + jbit) * s2 + b;
+                    const int qx = __ldg(g.sx + si), qy = __ldg(g.sy + si), qz = __ldg(g.sz + si);
+                    wc.leaf_tests += 2;
+                    hit = leaf(make_seg(ax, ay, az, qx, qy, qz), F, wc) &&
+                          leaf(make_seg(ex, ey, ez, qx, qy, qz), F, wc);
+                }
+                all = __all_sync(kFull, hit);
+            }
+            if (all) hidden |= 1u << jbit;
+        }
+    }
+    return hidden;
+}
+
+// True (warp-uniform) when every position of snapshots [t0, t1) is in range
+// and lies on the segment from position t0 to position t1 - 1 (scaled by k).
+__device__ __noinline__ bool tile_on_segment(const int *pos, long long t0, long long t1,
+                                             long long k)
+{
+    const int lane = threadIdx.x & 31;
+    const long long te = t1 - 1;
+    const long long A0 = k * pos[3 * t0], A1 = k * pos[3 * t0 + 1], A2 = k * pos[3 * t0 + 2];
+    const long long E0 = k * pos[3 * te], E1 = k * pos[3 * te + 1], E2 = k * pos[3 * te + 2];
+    bool ok = in_range(A0, A1, A2) && in_range(E0, E1, E2);
+    if (ok) {
+        const long long d0 = E0 - A0, d1 = E1 - A1, d2 = E2 - A2;
+        const long long dd = d0 * d0 + d1 * d1 + d2 * d2;
+        for (long long t = t0 + lane; t < t1 && ok; t += 32) {
+            const long long P0 = k * pos[3 * t], P1 = k * pos[3 * t + 1], P2 = k * pos[3 * t + 2];
+            if (!in_range(P0, P1, P2)) {
+                ok = false;
+                break;
+            }
+            const long long p0 = P0 - A0, p1 = P1 - A1, p2 = P2 - A2;
+            if (dd == 0) {
+                ok = p0 == 0 && p1 == 0 && p2 == 0;
+            } else {
+                const long long dot = p0 * d0 + p1 * d1 + p2 * d2;
+                ok = p1 * d2 == p2 * d1 && p2 * d0 == p0 * d2 && p0 * d1 == p1 * d0 &&
+                     dot >= 0 && dot <= dd;
+            }
+        }
+    }
+    return __all_sync(kFull, ok);
+}
+
 template <bool CACHE, class LeafFn>
 __device__ __forceinline__ void table_tile(const DevScenes &g, long long item, int TT,
                                            const int *rep, int *err, WalkCounters &wc,
-                                           LeafFn leaf, OccluderCache &cache)
+                                           LeafFn leaf, OccluderCache &cache, int *sblk)
 {
     const int lane = threadIdx.x & 31;
     const int sc = scene_of_item(g.desc, g.n_scenes, item);
@@ -153,81 +265,140 @@ __device__ __forceinline__ void table_tile(const DevScenes &g, long long item, i
     const long long k = 2LL * D.s;
     int prev_blk = -1;   // lane l: facet that last blocked facet 32c + l
     int prev_free = -1;  // lane l: sample of facet 32c + l seen at the previous snapshot
-    for (long long t = t0; t < t1; t++) {
-        if (rep && rep[2 * (D.snap0 + t) + side] != t) continue;   // copied later
-        uint32_t *row = D.table + ((size_t)t * 2 + side) * D.W;
-        const long long X0 = k * pos[3 * t], X1 = k * pos[3 * t + 1], X2 = k * pos[3 * t + 2];
-        if (!in_range(X0, X1, X2)) {
-            if (lane == 0) {
-                raise_error(err, IVM_ERR_RANGE);
-                row[c] = 0u;
+    // sblk[32 f + b]: the facet that last blocked sample b of facet 32c + f
+    const bool per_sample = CACHE && kTableSampleBlockers && s2 <= 32;
+    if (per_sample) {
+        for (int i = lane; i < kSampleSlots; i += 32) sblk[i] = -1;
+        __syncwarp();
+    }
+    for (long long u0 = t0; u0 < t1; u0 += kProofTile) {   // straight-stretch proofs
+        const long long u1 = min(u0 + (long long)kProofTile, t1);
+        bool proof = CACHE && kTableTileProof && u1 - u0 >= 3 &&
+                     tile_on_segment(pos, u0, u1, k);
+        unsigned hidden = 0;   // facets settled hidden for snapshots [u0, u1)
+        for (long long t = u0; t < u1; t++) {
+            if (rep && rep[2 * (D.snap0 + t) + side] != t) continue;   // copied later
+            uint32_t *row = D.table + ((size_t)t * 2 + side) * D.W;
+            const long long X0 = k * pos[3 * t], X1 = k * pos[3 * t + 1], X2 = k * pos[3 * t + 2];
+            if (!in_range(X0, X1, X2)) {
+                if (lane == 0) {
+                    raise_error(err, IVM_ERR_RANGE);
+                    row[c] = 0u;
+                }
+                continue;
             }
-            continue;
-        }
-        const int x = (int)X0, y = (int)X1, z = (int)X2;
-        const bool fr = has && ((long long)fnx * (x - fox) + (long long)fny * (y - foy) +
-                                (long long)fnz * (z - foz)) > 0;
-        unsigned fm = __ballot_sync(kFull, fr);
-        unsigned word = 0;
-        while (fm) {
-            if (s2 <= 32) {
-                const int G = 32 / s2;
-                const int cnt = min(G, __popc(fm));
-                const int gi = lane / s2, b = lane - gi * s2;
-                const bool mine = gi < cnt;
-                unsigned m = fm;
-                for (int q = 0; q < gi && q < 31; q++) m &= m - 1;
-                const int jbit = mine ? __ffs(m) - 1 : 0;
-                const int sidx = D.sample0 + (32 * c + jbit) * s2 + b;
-                const int tb = __shfl_sync(kFull, prev_blk, jbit);
-                const int pf = __shfl_sync(kFull, prev_free, jbit);
-                const int lead = D.facet0 + 32 * c + __shfl_sync(kFull, jbit, 0);
-                int myblk;
-                const unsigned alive = table_packet<CACHE>(g, D, mine, sidx, lead, x, y, z, tb,
-                                                           pf, gi, b, s2, err, wc, leaf, cache,
-                                                           myblk);
-                const unsigned smask = (s2 == 32) ? kFull : ((1u << s2) - 1u);
-                const unsigned gbits = (alive >> (gi * s2)) & smask;
-                const bool gvis = mine && gbits != 0u;
-                word |= __reduce_or_sync(kFull, (gvis && b == 0) ? (1u << jbit) : 0u);
-                if (CACHE) {
-                    // per facet: the blocker that hid it, or the sample it was seen through
-                    const int fs = gvis ? __ffs(gbits) - 1 : -1;
-                    for (int q = 0; q < cnt; q++) {
-                        const int jb = __shfl_sync(kFull, jbit, q * s2);
-                        const int nb = __shfl_sync(kFull, myblk, q * s2);
-                        const int f1 = __shfl_sync(kFull, fs, q * s2);
-                        if (lane == jb) {
-                            prev_free = f1;
-                            if (f1 < 0 && nb >= 0) prev_blk = nb;
+            const int x = (int)X0, y = (int)X1, z = (int)X2;
+            const bool fr = has && ((long long)fnx * (x - fox) + (long long)fny * (y - foy) +
+                                    (long long)fnz * (z - foz)) > 0;
+            unsigned fm = __ballot_sync(kFull, fr) & ~hidden;
+            unsigned word = 0;
+            if (CACHE && kTableBatchProbe) {
+                // one packet for the whole word: each facet seen at the previous
+                // snapshot walks the segment to the sample it was seen through;
+                // free ones are visible, the rest go on to their own packets
+                const bool pr = ((fm >> lane) & 1u) && prev_free >= 0;
+                const unsigned pm = __ballot_sync(kFull, pr);
+                if (pm) {
+                    int qx = 0, qy = 0, qz = 0;
+                    if (pr) {
+                        const int si = D.sample0 + jl * s2 + prev_free;
+                        qx = __ldg(g.sx + si); qy = __ldg(g.sy + si); qz = __ldg(g.sz + si);
+                    }
+                    wc.segments += pr;
+                    Seg sg = make_seg(x, y, z, qx, qy, qz);
+                    const int lead = __ffs(pm) - 1;
+                    const float dirx = (float)__shfl_sync(kFull, sg.dx, lead);
+                    const float diry = (float)__shfl_sync(kFull, sg.dy, lead);
+                    const float dirz = (float)__shfl_sync(kFull, sg.dz, lead);
+                    int myblk = -1;
+                    const unsigned freem = pm & occlude<CACHE, LeafFn, false>(
+                        sg, pm, g.nodes, g.leaf, D.root, dirx, diry, dirz, 4 * D.n + 16, err, wc,
+                        leaf, cache, myblk);
+                    word |= freem;
+                    fm &= ~freem;
+                    if (pr && !((freem >> lane) & 1u)) {
+                        if (myblk >= 0) {
+                            prev_blk = myblk;
+                            if (per_sample) sblk[32 * lane + prev_free] = myblk;
+                        }
+                        prev_free = -1;
+                    }
+                    if (per_sample) __syncwarp();
+                }
+            }
+            while (fm) {
+                if (s2 <= 32) {
+                    const int G = 32 / s2;
+                    const int cnt = min(G, __popc(fm));
+                    const int gi = lane / s2, b = lane - gi * s2;
+                    const bool mine = gi < cnt;
+                    unsigned m = fm;
+                    for (int q = 0; q < gi && q < 31; q++) m &= m - 1;
+                    const int jbit = mine ? __ffs(m) - 1 : 0;
+                    const int sidx = D.sample0 + (32 * c + jbit) * s2 + b;
+                    int tb = __shfl_sync(kFull, prev_blk, jbit);
+                    if (per_sample && mine) {
+                        const int v = sblk[32 * jbit + b];
+                        if (v >= 0) tb = v;
+                    }
+                    const int pf = __shfl_sync(kFull, prev_free, jbit);
+                    const int lead = D.facet0 + 32 * c + __shfl_sync(kFull, jbit, 0);
+                    int myblk;
+                    const unsigned alive = table_packet<CACHE>(g, D, mine, sidx, lead, x, y, z, tb,
+                                                               pf, gi, b, s2, err, wc, leaf, cache,
+                                                               myblk);
+                    if (per_sample) {
+                        if (mine && myblk >= 0) sblk[32 * jbit + b] = myblk;
+                        __syncwarp();
+                    }
+                    const unsigned smask = (s2 == 32) ? kFull : ((1u << s2) - 1u);
+                    const unsigned gbits = (alive >> (gi * s2)) & smask;
+                    const bool gvis = mine && gbits != 0u;
+                    word |= __reduce_or_sync(kFull, (gvis && b == 0) ? (1u << jbit) : 0u);
+                    if (CACHE) {
+                        // per facet: the blocker that hid it, or the sample it was seen through
+                        const int fs = gvis ? __ffs(gbits) - 1 : -1;
+                        for (int q = 0; q < cnt; q++) {
+                            const int jb = __shfl_sync(kFull, jbit, q * s2);
+                            const int nb = __shfl_sync(kFull, myblk, q * s2);
+                            const int f1 = __shfl_sync(kFull, fs, q * s2);
+                            if (lane == jb) {
+                                prev_free = f1;
+                                if (f1 < 0 && nb >= 0) prev_blk = nb;
+                            }
                         }
                     }
-                }
-                for (int q = 0; q < cnt; q++) fm &= fm - 1;
-            } else {
-                const int jbit = __ffs(fm) - 1;
-                fm &= fm - 1;
-                const int jlocal = 32 * c + jbit;
-                const int tb = __shfl_sync(kFull, prev_blk, jbit);
-                int last = -1;
-                bool vis = false;
-                for (int b0 = 0; b0 < s2; b0 += 32) {
-                    const int b = b0 + lane;
-                    int myblk;
-                    const unsigned alive = table_packet<CACHE>(
-                        g, D, b < s2, D.sample0 + jlocal * s2 + b, D.facet0 + jlocal, x, y, z,
-                        tb, -1, 0, b, 32, err, wc, leaf, cache, myblk);
-                    if (alive) {
-                        vis = true;
-                        break;
+                    for (int q = 0; q < cnt; q++) fm &= fm - 1;
+                } else {
+                    const int jbit = __ffs(fm) - 1;
+                    fm &= fm - 1;
+                    const int jlocal = 32 * c + jbit;
+                    const int tb = __shfl_sync(kFull, prev_blk, jbit);
+                    int last = -1;
+                    bool vis = false;
+                    for (int b0 = 0; b0 < s2; b0 += 32) {
+                        const int b = b0 + lane;
+                        int myblk;
+                        const unsigned alive = table_packet<CACHE>(
+                            g, D, b < s2, D.sample0 + jlocal * s2 + b, D.facet0 + jlocal, x, y, z,
+                            tb, -1, 0, b, 32, err, wc, leaf, cache, myblk);
+                        if (alive) {
+                            vis = true;
+                            break;
+                        }
+                        last = __shfl_sync(kFull, myblk, 0);
                     }
-                    last = __shfl_sync(kFull, myblk, 0);
+                    if (vis) word |= 1u << jbit;
+                    else if (CACHE && lane == jbit && last >= 0) prev_blk = last;
                 }
-                if (vis) word |= 1u << jbit;
-                else if (CACHE && lane == jbit && last >= 0) prev_blk = last;
+            }
+            if (lane == 0) row[c] = word;
+            if (proof && t + 2 < u1) {   // once, after the first traced snapshot
+                proof = false;
+                hidden = tile_hidden(g, D, c, prev_blk, pos + 3 * u0, pos + 3 * (u1 - 1), (int)k,
+                                     per_sample ? sblk : nullptr, wc, leaf);
             }
         }
-        if (lane == 0) row[c] = word;
     }
 }
 
@@ -272,12 +443,14 @@ k_table(DevScenes g, long long total_items, long long all_items, int TT,
                         const int *rep, unsigned long long *work, unsigned long long *ctr,
                         int *err)
 {
+    extern __shared__ int smem_blk[];
     WalkCounters wc;
     LeafFn leaf;
     OccluderCache cache;
     const int lane = threadIdx.x & 31;
+    int *sblk = CACHE ? smem_blk + (threadIdx.x >> 5) * kSampleSlots : nullptr;
     auto run = [&](long long it) {
-        if (it < total_items) table_tile<CACHE>(g, it, TT, rep, err, wc, leaf, cache);
+        if (it < total_items) table_tile<CACHE>(g, it, TT, rep, err, wc, leaf, cache, sblk);
         else los_item<CACHE>(g, it - total_items, err, wc, leaf, cache);
     };
     if (!PERSIST) {
@@ -361,15 +534,16 @@ static void launch_one(const DevScenes &g, long long items, long long all, int T
 {
     const int threads = 32 * cfg.warps_per_block;
     auto kern = k_table<PERSIST, CACHE, LeafFn>;
+    const size_t smem = CACHE ? sizeof(int) * kSampleSlots * cfg.warps_per_block : 0;
     if (PERSIST) {
         int per_sm = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
         int blocks = cfg.n_sm * (per_sm > 0 ? per_sm : 1);
         cudaMemsetAsync(work, 0, sizeof(unsigned long long), st);
-        kern<<<blocks, threads, 0, st>>>(g, items, all, TT, rep, work, ctr, err);
+        kern<<<blocks, threads, smem, st>>>(g, items, all, TT, rep, work, ctr, err);
     } else {
         long long blocks = (all + cfg.warps_per_block - 1) / cfg.warps_per_block;
-        kern<<<(unsigned)blocks, threads, 0, st>>>(g, items, all, TT, rep, work, ctr, err);
+        kern<<<(unsigned)blocks, threads, smem, st>>>(g, items, all, TT, rep, work, ctr, err);
     }
 }
 

@@ -77,6 +77,8 @@ struct CutFilter {
         const int c = __ldg(ncl + id);
         return c < 0 || !((done >> c) & 1ull);
     }
+    __device__ __forceinline__ void grow(float &, float &, float &, float &, float &,
+                                         float &) const {}
 };
 
 // The pair's centroid segment in 2x scaled units (2 o + u + v is twice a

@@ -44,6 +44,7 @@ namespace ivm {
 constexpr bool kTableProbe = true;
 constexpr bool kTableLru = true;
 constexpr bool kTableTileProof = true;
+constexpr bool kTableSweep = true;   // also settle visible facets by a swept walk
 constexpr bool kTableBatchProbe = true;
 // Per-sample temporal blockers (shared memory, 32 facets x 32 samples per warp).
 constexpr bool kTableSampleBlockers = true;
@@ -205,6 +206,99 @@ __device__ __noinline__ unsigned tile_hidden(const DevScenes &g, const SceneDesc
     return hidden;
 }
 
+// Swept walk: the segments from the points a of [A, E] to q fill the
+// triangle T = conv(A, E, q), and T lies in the segment [A, q] moved by
+// every vector between 0 and E - A (per axis); so a box meets some open
+// segment a-q only if segment A-q meets the box widened by that range.
+struct SweepFilter {
+    float lx, ly, lz, hx, hy, hz;   // lo -= max(0, E - A), hi -= min(0, E - A)
+    __device__ __forceinline__ bool node(int) const { return true; }
+    __device__ __forceinline__ void grow(float &ax, float &ay, float &az, float &bx, float &by,
+                                         float &bz) const
+    {
+        // directed rounding keeps the widened box a superset
+        ax = __fsub_rd(ax, lx); ay = __fsub_rd(ay, ly); az = __fsub_rd(az, lz);
+        bx = __fadd_ru(bx, hx); by = __fadd_ru(by, hy); bz = __fadd_ru(bz, hz);
+    }
+};
+
+// Leaf test of the swept walk: false only when facet F provably blocks no
+// open segment a-q, a in [A, E] (the Seg holds A and q - A, the functor E).
+// Along [A, E] the plane side n.(a - o) and the four edge orientations
+// orient(a, f_k, f_k+1, q) are affine in a, so a sign shared by both ends
+// holds all along.  F blocks a-q only if a is strictly on the other side of
+// F's plane from q (or, with q on the plane, the segment lies in it) and the
+// four edge orientations are all >= 0 or all <= 0.
+struct SweepLeaf {
+    int ex, ey, ez;
+    __device__ __forceinline__ bool operator()(const Seg &s, const Leaf &L, WalkCounters &wc) const
+    {
+        const int qx = s.px + s.dx, qy = s.py + s.dy, qz = s.pz + s.dz;
+        const long long sq = (long long)L.nx * (qx - L.ox) + (long long)L.ny * (qy - L.oy) +
+                             (long long)L.nz * (qz - L.oz);
+        const long long sa = (long long)L.nx * (s.px - L.ox) + (long long)L.ny * (s.py - L.oy) +
+                             (long long)L.nz * (s.pz - L.oz);
+        const long long se = (long long)L.nx * (ex - L.ox) + (long long)L.ny * (ey - L.oy) +
+                             (long long)L.nz * (ez - L.oz);
+        if (sq == 0) return !((sa > 0 && se > 0) || (sa < 0 && se < 0));
+        if (sq > 0 ? (sa >= 0 && se >= 0) : (sa <= 0 && se <= 0)) return false;
+        unsigned neg = 0xF, pos = 0xF;   // edges strictly negative / positive at both ends
+        for (int end = 0; end < 2; end++) {
+            const int px = end ? ex : s.px, py = end ? ey : s.py, pz = end ? ez : s.pz;
+            const float dx = (float)(qx - px), dy = (float)(qy - py), dz = (float)(qz - pz);
+            const float f0x = (float)(L.ox - px), f0y = (float)(L.oy - py), f0z = (float)(L.oz - pz);
+            const float f1x = f0x + (float)L.ux, f1y = f0y + (float)L.uy, f1z = f0z + (float)L.uz;
+            const float f2x = f1x + (float)L.vx, f2y = f1y + (float)L.vy, f2z = f1z + (float)L.vz;
+            const float f3x = f0x + (float)L.vx, f3y = f0y + (float)L.vy, f3z = f0z + (float)L.vz;
+            const int e0 = orient_filtered(f0x, f0y, f0z, f1x, f1y, f1z, dx, dy, dz);
+            const int e1 = orient_filtered(f1x, f1y, f1z, f2x, f2y, f2z, dx, dy, dz);
+            const int e2 = orient_filtered(f2x, f2y, f2z, f3x, f3y, f3z, dx, dy, dz);
+            const int e3 = orient_filtered(f3x, f3y, f3z, f0x, f0y, f0z, dx, dy, dz);
+            neg &= (e0 < 0) | ((e1 < 0) << 1) | ((e2 < 0) << 2) | ((e3 < 0) << 3);
+            pos &= (e0 > 0) | ((e1 > 0) << 1) | ((e2 > 0) << 2) | ((e3 > 0) << 3);
+        }
+        (void)wc;
+        return !(neg && pos);   // undecided signs (0) never rule a case out
+    }
+};
+
+// Facets of word c (lanes with pf >= 0: seen through sample pf) that face
+// both A = k pa and E = k pe strictly and whose segment to sample pf no facet
+// can block from any point of [A, E]: visible at every snapshot of the
+// stretch (facing is affine along [A, E] too).  One swept walk for the word.
+__device__ __noinline__ unsigned tile_shown(const DevScenes &g, const SceneDesc &D, int c,
+                                            int pf, const int *pa, const int *pe, int k, int *err,
+                                            WalkCounters &wc)
+{
+    const int lane = threadIdx.x & 31;
+    const int jl = 32 * c + lane;
+    const int ax = k * pa[0], ay = k * pa[1], az = k * pa[2];   // in range: checked
+    const int ex = k * pe[0], ey = k * pe[1], ez = k * pe[2];
+    bool cand = false;
+    int qx = 0, qy = 0, qz = 0;
+    if (jl < D.n && pf >= 0) {
+        const Leaf L = load_leaf(g.leaf, D.facet0 + jl);
+        cand = front_of(L, ax, ay, az) && front_of(L, ex, ey, ez);
+        const int si = D.sample0 + jl * D.s * D.s + pf;
+        qx = __ldg(g.sx + si); qy = __ldg(g.sy + si); qz = __ldg(g.sz + si);
+    }
+    const unsigned pm = __ballot_sync(kFull, cand);
+    if (!pm) return 0;
+    Seg sg = make_seg(ax, ay, az, qx, qy, qz);
+    finish_seg(sg);
+    const int lead = __ffs(pm) - 1;
+    const float dirx = (float)__shfl_sync(kFull, sg.dx, lead);
+    const float diry = (float)__shfl_sync(kFull, sg.dy, lead);
+    const float dirz = (float)__shfl_sync(kFull, sg.dz, lead);
+    const int gx = ex - ax, gy = ey - ay, gz = ez - az;
+    const SweepFilter f{(float)max(gx, 0), (float)max(gy, 0), (float)max(gz, 0),
+                        (float)-min(gx, 0), (float)-min(gy, 0), (float)-min(gz, 0)};
+    int blocker, myblk = -1;
+    wc.segments += cand;
+    return walk_packet(sg, pm, g.nodes, g.leaf, D.root, dirx, diry, dirz, 4 * D.n + 16, err, wc,
+                       SweepLeaf{ex, ey, ez}, blocker, myblk, f);
+}
+
 // True (warp-uniform) when every position of snapshots [t0, t1) is in range
 // and lies on the segment from position t0 to position t1 - 1 (scaled by k).
 __device__ __noinline__ bool tile_on_segment(const int *pos, long long t0, long long t1,
@@ -276,6 +370,7 @@ __device__ __forceinline__ void table_tile(const DevScenes &g, long long item, i
         bool proof = CACHE && kTableTileProof && u1 - u0 >= 3 &&
                      tile_on_segment(pos, u0, u1, k);
         unsigned hidden = 0;   // facets settled hidden for snapshots [u0, u1)
+        unsigned shown = 0;    // facets settled visible for snapshots [u0, u1)
         for (long long t = u0; t < u1; t++) {
             if (rep && rep[2 * (D.snap0 + t) + side] != t) continue;   // copied later
             uint32_t *row = D.table + ((size_t)t * 2 + side) * D.W;
@@ -290,8 +385,8 @@ __device__ __forceinline__ void table_tile(const DevScenes &g, long long item, i
             const int x = (int)X0, y = (int)X1, z = (int)X2;
             const bool fr = has && ((long long)fnx * (x - fox) + (long long)fny * (y - foy) +
                                     (long long)fnz * (z - foz)) > 0;
-            unsigned fm = __ballot_sync(kFull, fr) & ~hidden;
-            unsigned word = 0;
+            unsigned fm = __ballot_sync(kFull, fr) & ~hidden & ~shown;
+            unsigned word = shown;
             if (CACHE && kTableBatchProbe) {
                 // one packet for the whole word: each facet seen at the previous
                 // snapshot walks the segment to the sample it was seen through;
@@ -397,6 +492,9 @@ __device__ __forceinline__ void table_tile(const DevScenes &g, long long item, i
                 proof = false;
                 hidden = tile_hidden(g, D, c, prev_blk, pos + 3 * u0, pos + 3 * (u1 - 1), (int)k,
                                      per_sample ? sblk : nullptr, wc, leaf);
+                if (kTableSweep)
+                    shown = tile_shown(g, D, c, prev_free, pos + 3 * u0, pos + 3 * (u1 - 1),
+                                       (int)k, err, wc);
             }
         }
     }

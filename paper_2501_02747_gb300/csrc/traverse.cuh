@@ -222,9 +222,13 @@ __device__ __forceinline__ void flush_counters(const WalkCounters &wc, unsigned 
 // 2 * nodes + 2); when it runs out, IVM_ERR_TIMEOUT is raised.
 // `root` may be any node (or ~facet), so a walk can cover one subtree.
 // Walk filters: filt.node(index) says whether the walk enters an internal
-// node; NoFilter enters every node.
+// node, filt.grow widens each child box before its test; NoFilter enters
+// every node and keeps the boxes.
 struct NoFilter {
     __device__ __forceinline__ bool node(int) const { return true; }
+    // widen a child box before it is tested (swept walks)
+    __device__ __forceinline__ void grow(float &, float &, float &, float &, float &,
+                                         float &) const {}
 };
 
 template <class LeafFn, class Filter = NoFilter>
@@ -258,6 +262,8 @@ __device__ __forceinline__ unsigned walk_packet(const Seg &s, unsigned alive, co
             float4 A = __ldg(np), B = __ldg(np + 1), C = __ldg(np + 2);
             int4 D = __ldg(reinterpret_cast<const int4 *>(np + 3));
             bool me = ((alive >> lane) & 1u) && filt.node(node);
+            filt.grow(A.x, A.y, A.z, A.w, B.x, B.y);
+            filt.grow(B.z, B.w, C.x, C.y, C.z, C.w);
             bool hl = me && seg_box(s, A.x, A.y, A.z, A.w, B.x, B.y);
             bool hr = me && seg_box(s, B.z, B.w, C.x, C.y, C.z, C.w);
             wc.node_tests += 2 * me;

@@ -66,6 +66,44 @@ __device__ __forceinline__ unsigned occlude_ranked(Seg &s, unsigned alive, const
     return alive;
 }
 
+// Blocked sets are convex: for a convex facet F and a fixed end q, the
+// points p from which the open segment p-q meets F form a convex set
+// ({q + L (f - q) : f in F, L > 1}), and so do the points q for a fixed p.
+// A facet's samples lie in the convex hull of its four corner samples.  So
+// if F blocks the 16 segments between the corner samples of facets i and j,
+// it blocks every sample segment between them and M_ij = 0: for each corner
+// p_c the q-set contains j's corners, hence all of j's samples; then for
+// each sample q the p-set contains i's corners, hence all of i's samples.
+// Candidates F are the warp's recent occluders; lanes 0-15 test one, 16-31
+// another, with the same exact facet test as everywhere else.
+constexpr bool kMatrixCornerProof = true;
+
+template <class LeafFn>
+__device__ __noinline__ bool corners_blocked(const DevScenes &g, int baseI, int baseJ, int s,
+                                             int f0, int f1, int f2, int f3, WalkCounters &wc,
+                                             LeafFn leaf)
+{
+    const int lane = threadIdx.x & 31;
+    const int l = s - 1;   // corner samples: a, b in {0, s - 1}, index a s + b
+    const int ka = ((lane & 1) ? l * s : 0) + ((lane & 2) ? l : 0);
+    const int kb = ((lane & 4) ? l * s : 0) + ((lane & 8) ? l : 0);
+    const Seg sg = make_seg(__ldg(g.sx + baseI + ka), __ldg(g.sy + baseI + ka),
+                            __ldg(g.sz + baseI + ka), __ldg(g.sx + baseJ + kb),
+                            __ldg(g.sy + baseJ + kb), __ldg(g.sz + baseJ + kb));
+    for (int pass = 0; pass < 2; pass++) {
+        const int F = (lane >> 4) ? (pass ? f3 : f1) : (pass ? f2 : f0);
+        bool hit = false;
+        if (F >= 0) {
+            wc.leaf_tests++;
+            hit = leaf(sg, load_leaf(g.leaf, F), wc);
+        }
+        const unsigned hm = __ballot_sync(kFull, hit);
+        if ((hm & 0xFFFFu) == 0xFFFFu || (hm >> 16) == 0xFFFFu) return true;
+        if ((pass ? f2 : f0) < 0) break;
+    }
+    return false;
+}
+
 template <bool CACHE, bool LEARN, class LeafFn>
 __device__ __forceinline__ void decide_pair(const DevScenes &g, int gi, int gj,
                                             const LearnedDev &lrn, unsigned long long rk,
@@ -83,7 +121,12 @@ __device__ __forceinline__ void decide_pair(const DevScenes &g, int gi, int gj,
     const float diry = (float)(2 * (Lj.oy - Li.oy) + Lj.uy + Lj.vy - Li.uy - Li.vy);
     const float dirz = (float)(2 * (Lj.oz - Li.oz) + Lj.uz + Lj.vz - Li.uz - Li.vz);
     const int budget = 4 * D.n + 16;
+    if (CACHE && kMatrixCornerProof && cache.f[0] >= 0 &&
+        corners_blocked(g, baseI, baseJ, s, cache.f[0], cache.f[1], cache.f[2], cache.f[3], wc,
+                        leaf))
+        return;
     bool visible = false;
+    bool retried = false;
     for (int b0 = 0; b0 < total; b0 += 32) {
         const int idx = b0 + lane;
         const bool valid = idx < total;
@@ -109,6 +152,12 @@ __device__ __forceinline__ void decide_pair(const DevScenes &g, int gi, int gj,
         if (alive) {
             visible = true;
             break;
+        }
+        // the first blocked packet may have brought a new occluder to the front
+        if (CACHE && kMatrixCornerProof && !retried && b0 + 32 < total) {
+            retried = true;
+            const int f = cache.f[0];
+            if (f >= 0 && corners_blocked(g, baseI, baseJ, s, f, -1, -1, -1, wc, leaf)) return;
         }
     }
     if (visible && lane == 0) {

@@ -50,7 +50,7 @@ constexpr bool kTableBatchProbe = true;
 constexpr bool kTableSampleBlockers = true;
 constexpr int kSampleSlots = 32 * 32;
 // Snapshots per straight-stretch proof (a work item may hold several).
-constexpr int kProofTile = 32;
+constexpr int kProofTile = 16;
 
 __device__ __forceinline__ int scene_of_snap(const SceneDesc *desc, int n_scenes, long long T)
 {
@@ -371,6 +371,16 @@ __device__ __forceinline__ void table_tile(const DevScenes &g, long long item, i
                      tile_on_segment(pos, u0, u1, k);
         unsigned hidden = 0;   // facets settled hidden for snapshots [u0, u1)
         unsigned shown = 0;    // facets settled visible for snapshots [u0, u1)
+        if (proof && u0 > t0) {
+            // what the previous stretch left (each facet's blockers or free
+            // sample) is tried first; the facets it settles need no snapshot
+            hidden = tile_hidden(g, D, c, prev_free < 0 ? prev_blk : -1, pos + 3 * u0,
+                                 pos + 3 * (u1 - 1), (int)k, per_sample ? sblk : nullptr, wc,
+                                 leaf);
+            if (kTableSweep)
+                shown = tile_shown(g, D, c, prev_free, pos + 3 * u0, pos + 3 * (u1 - 1), (int)k,
+                                   err, wc);
+        }
         for (long long t = u0; t < u1; t++) {
             if (rep && rep[2 * (D.snap0 + t) + side] != t) continue;   // copied later
             uint32_t *row = D.table + ((size_t)t * 2 + side) * D.W;
@@ -490,11 +500,13 @@ __device__ __forceinline__ void table_tile(const DevScenes &g, long long item, i
             if (lane == 0) row[c] = word;
             if (proof && t + 2 < u1) {   // once, after the first traced snapshot
                 proof = false;
-                hidden = tile_hidden(g, D, c, prev_blk, pos + 3 * u0, pos + 3 * (u1 - 1), (int)k,
-                                     per_sample ? sblk : nullptr, wc, leaf);
+                const bool open = !(((hidden | shown) >> lane) & 1u);   // not settled yet
+                hidden |= tile_hidden(g, D, c, open && prev_free < 0 ? prev_blk : -1,
+                                      pos + 3 * u0, pos + 3 * (u1 - 1), (int)k,
+                                      per_sample ? sblk : nullptr, wc, leaf);
                 if (kTableSweep)
-                    shown = tile_shown(g, D, c, prev_free, pos + 3 * u0, pos + 3 * (u1 - 1),
-                                       (int)k, err, wc);
+                    shown |= tile_shown(g, D, c, open ? prev_free : -1, pos + 3 * u0,
+                                        pos + 3 * (u1 - 1), (int)k, err, wc);
             }
         }
     }

@@ -78,6 +78,12 @@ def lib():
         L.oracle_splitmix64.restype = ctypes.c_uint64
         L.oracle_fp_weight.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]
         L.oracle_fp_weight.restype = ctypes.c_uint64
+        L.oracle_first_blocker_pts.argtypes = [_i32p, ctypes.c_int32, ctypes.c_int32, _i64p,
+                                               _i64p]
+        L.oracle_first_blocker_pts.restype = ctypes.c_int32
+        L.oracle_first_blocker.argtypes = [_i32p, ctypes.c_int32, ctypes.c_int32, _i32p,
+                                           ctypes.c_int32]
+        L.oracle_first_blocker.restype = ctypes.c_int32
         _lib = L
     return _lib
 
@@ -251,3 +257,93 @@ def splitmix64(x: int) -> int:
 
 def fp_weight(c: int, m: int, f: int) -> int:
     return int(lib().oracle_fp_weight(c, m, f))
+
+
+# ---------------------------------------------------- visibility ranges
+
+RANGE_DTYPE = np.dtype([("side", "<i4"), ("facet", "<i4"), ("begin", "<i8"), ("end", "<i8"),
+                        ("block_before", "<i4"), ("block_after", "<i4")])
+
+
+def first_blocker_pts(facets, s, P, Q) -> int:
+    """First facet met by the open segment P -> Q (scaled points), or -1."""
+    F = _facets(facets)
+    P = np.ascontiguousarray(P, dtype=np.int64)
+    Q = np.ascontiguousarray(Q, dtype=np.int64)
+    return int(lib().oracle_first_blocker_pts(_p(F, _i32p), F.shape[0], s, _p(P, _i64p),
+                                              _p(Q, _i64p)))
+
+
+def first_blocker(facets, s, X, j) -> int:
+    """First facet met by the segment from X (cm) to facet j's centre sample, or -1."""
+    F = _facets(facets)
+    X = np.ascontiguousarray(X, dtype=np.int32)
+    return int(lib().oracle_first_blocker(_p(F, _i32p), F.shape[0], s, _p(X, _i32p), int(j)))
+
+
+def _front(F, s, X, j):
+    """Strict facing of facet j towards the point X (cm) [Sec. II-B, Eq. (2)]."""
+    o, u, v = (F[j, 0:3].astype(object), F[j, 3:6].astype(object), F[j, 6:9].astype(object))
+    n = (u[1] * v[2] - u[2] * v[1], u[2] * v[0] - u[0] * v[2], u[0] * v[1] - u[1] * v[0])
+    d = [int(X[k]) - int(o[k]) for k in range(3)]
+    return n[0] * d[0] + n[1] * d[1] + n[2] * d[2] > 0
+
+
+def run_lengths(tab, n):
+    """The maximal runs [begin, end) of set bits of every column (side, facet j)
+    of a table [S][2][W], sorted by side, facet, begin (Blockage fields 0)."""
+    tab = np.ascontiguousarray(tab, dtype=np.uint32)
+    bits = np.unpackbits(tab.view(np.uint8), axis=-1, bitorder="little")[..., :n]  # [S][2][n]
+    recs = []
+    for side in range(2):
+        for j in range(n):
+            col = bits[:, side, j].astype(np.int8)
+            edge = np.diff(np.concatenate(([0], col, [0])))
+            starts = np.nonzero(edge == 1)[0]
+            ends = np.nonzero(edge == -1)[0]
+            for b, e in zip(starts, ends):
+                recs.append((side, j, int(b), int(e), 0, 0))
+    return np.array(recs, dtype=RANGE_DTYPE)
+
+
+def visibility_ranges(facets, s, tx, rx, tab, n_facets=None, threads=None):
+    """Visibility ranges of a table [S][2][W] (Sec. III-C, Tables III-IV) and
+    their coherence-time sums (Sec. III-D, Eq. (8)-(9)).
+
+    A range is a maximal run [begin, end) of snapshots in which bit j of the
+    side's row is set (side 0: Tx rows, the transmitter as parent node; side 1:
+    Rx rows).  Its creation and suppression points are begin and end.  The
+    Blockage column: at snapshot begin - 1 and at snapshot end, the building of
+    the first facet on the segment from the source to facet j's centre sample
+    (step 8 of ivm_oracle.c); -1 where the route starts or ends, -2 where facet
+    j does not face the source.  Returns (records sorted by side, facet,
+    begin; ranges[2]; snapshots[2]) with snapshots[x] the summed range lengths,
+    so that the mean range duration is dt * snapshots[x] / ranges[x].  The
+    Blockage entries are facet indices (the paper's column names the facet's
+    building, facets[:, 9])."""
+    F = _facets(facets)
+    n = F.shape[0] if n_facets is None else n_facets
+    S = np.asarray(tab).shape[0]
+    pos = [np.ascontiguousarray(tx, dtype=np.int32).reshape(-1, 3),
+           np.ascontiguousarray(rx, dtype=np.int32).reshape(-1, 3)]
+    out = run_lengths(tab, n)
+
+    def blockage(side, j, t):
+        if t < 0 or t >= S:
+            return -1
+        X = pos[side][t]
+        if not _front(F, s, X, j):
+            return -2
+        return first_blocker(F, s, X, j)   # >= 0: a hidden facing facet is blocked
+
+    def fill(k):
+        r = out[k]
+        out[k]["block_before"] = blockage(int(r["side"]), int(r["facet"]), int(r["begin"]) - 1)
+        out[k]["block_after"] = blockage(int(r["side"]), int(r["facet"]), int(r["end"]))
+
+    with ThreadPoolExecutor(_threads(threads)) as ex:
+        list(ex.map(fill, range(len(out))))
+    ranges = np.array([np.sum(out["side"] == x) for x in range(2)], dtype=np.int64)
+    snaps = np.array([np.sum((out["end"] - out["begin"])[out["side"] == x]) for x in range(2)],
+                     dtype=np.int64)
+    return out, ranges, snaps

@@ -44,6 +44,13 @@
  *  7. Traditional per-snapshot method [Sec. IV-B, brute-force image tree per
  *     location]: the same path sets with every hop's visibility recomputed
  *     from geometry at every snapshot, no cached matrix.
+ *  8. Blockage [Sec. III-C, Tables III-IV, "Blockage" column]: the first
+ *     facet the segment from a source point to facet j's centre sample
+ *     (a = b = floor(s/2)) meets, i.e. the hit with the smallest parameter l
+ *     in (0,1) (the infimum of the hit parameters, 0 when the segment starts
+ *     inside a coplanar facet); ties go to the lower facet index.  The
+ *     visibility ranges themselves (runs of a table bit along the route,
+ *     Tables III-IV) are read off the table in oracle/__init__.py.
  *
  * Bit layout of rows: bit j of a row is word j >> 5, bit j & 31 (LSB first);
  * W = ceil(N / 32) words per row; padding bits are 0.
@@ -127,7 +134,17 @@ static int frac_le(i128 a, i128 b, i128 c, i128 d) { return a * d <= c * b; }
  * it is found by clipping against the three edge half-planes in the
  * projection that drops the normal's dominant axis.  The open segment meets
  * the triangle iff lo <= hi, lo < 1 and hi > 0. */
+static int coplanar_clip(V P, V Q, V A, V B, V C, i128 *lo_num, i128 *lo_den);
+
 static int coplanar_hit(V P, V Q, V A, V B, V C)
+{
+    i128 ln, ld;
+    return coplanar_clip(P, Q, A, B, C, &ln, &ld);
+}
+
+/* The coplanar test of coplanar_hit; also returns the clip interval's lower
+ * end lo = lo_num / lo_den (lo_den > 0, lo >= 0). */
+static int coplanar_clip(V P, V Q, V A, V B, V C, i128 *lo_num, i128 *lo_den)
 {
     V n = cross(sub(B, A), sub(C, A));
     i128 ax = n.x < 0 ? -n.x : n.x, ay = n.y < 0 ? -n.y : n.y, az = n.z < 0 ? -n.z : n.z;
@@ -164,6 +181,8 @@ static int coplanar_hit(V P, V Q, V A, V B, V C)
             return 0;
         }
     }
+    *lo_num = lo_n;
+    *lo_den = lo_d;
     return frac_le(lo_n, lo_d, hi_n, hi_d) && frac_lt(lo_n, lo_d, 1, 1) && frac_lt(0, 1, hi_n, hi_d);
 }
 
@@ -182,6 +201,44 @@ static int seg_hits_tri(V P, V Q, V A, V B, V C)
         return (e1 >= 0 && e2 >= 0 && e3 >= 0) || (e1 <= 0 && e2 <= 0 && e3 <= 0);
     }
     return coplanar_hit(P, Q, A, B, C);
+}
+
+static i128 gcd128(i128 a, i128 b)
+{
+    if (a < 0) a = -a;
+    if (b < 0) b = -b;
+    while (b) { i128 t = a % b; a = b; b = t; }
+    return a;
+}
+
+/* step 8: the first facet the open segment P -> Q meets, or -1.  A crossing
+ * of triangle ABC's plane is at l = oP / (oP - oQ), oP and oQ the sides of P
+ * and Q against the plane (normal divided by the gcd of its components, so
+ * that the cross-multiplied comparisons stay within 128 bits); a coplanar hit
+ * starts at the clip interval's lower end. */
+static int32_t first_blocker(const Facet *F, int32_t n, V P, V Q)
+{
+    int32_t best = -1;
+    i128 bn = 1, bd = 1;
+    for (int32_t k = 0; k < n; k++)
+        for (int t = 0; t < 2; t++) {
+            V A = F[k].tri[t][0], B = F[k].tri[t][1], C = F[k].tri[t][2];
+            if (!seg_hits_tri(P, Q, A, B, C)) continue;
+            V nr = cross(sub(B, A), sub(C, A));
+            i128 g = gcd128(gcd128(nr.x, nr.y), nr.z);
+            nr = mk(nr.x / g, nr.y / g, nr.z / g);
+            i128 oP = dot(nr, sub(P, A)), oQ = dot(nr, sub(Q, A));
+            i128 ln = 0, ld = 1;
+            if (oP == 0 && oQ == 0) {
+                coplanar_clip(P, Q, A, B, C, &ln, &ld);
+            } else {
+                ln = oP;
+                ld = oP - oQ;
+                if (ld < 0) { ln = -ln; ld = -ld; }
+            }
+            if (best < 0 || frac_lt(ln, ld, bn, bd)) { best = k; bn = ln; bd = ld; }
+        }
+    return best;
 }
 
 static int blocked(const Facet *F, int32_t n, V P, V Q)
@@ -274,6 +331,26 @@ OR_EXPORT int oracle_los(const int32_t *facets, int32_t n, int32_t s, const int3
 {
     Facet *F = load_facets(facets, n, s);
     int r = !blocked(F, n, point_of(A, s), point_of(B, s));
+    free(F);
+    return r;
+}
+
+/* step 8 on scaled points P, Q; and from the source point X (cm) to the
+ * centre sample of facet j. */
+OR_EXPORT int32_t oracle_first_blocker_pts(const int32_t *facets, int32_t n, int32_t s,
+                                           const int64_t *P, const int64_t *Q)
+{
+    Facet *F = load_facets(facets, n, s);
+    int32_t r = first_blocker(F, n, mk(P[0], P[1], P[2]), mk(Q[0], Q[1], Q[2]));
+    free(F);
+    return r;
+}
+
+OR_EXPORT int32_t oracle_first_blocker(const int32_t *facets, int32_t n, int32_t s,
+                                       const int32_t *X, int32_t j)
+{
+    Facet *F = load_facets(facets, n, s);
+    int32_t r = first_blocker(F, n, point_of(X, s), sample(&F[j], s, s / 2, s / 2));
     free(F);
     return r;
 }

@@ -139,3 +139,58 @@ def rect_blocked(facets, scale, P, Q):
         if rect_seg_hits(P, Q, rect_of_facet(list(map(int, f)), scale)):
             return True
     return False
+
+
+def frac_first_hit(P, Q, A, B, C):
+    """Smallest (infimum) parameter l in [0, 1) at which the open segment P->Q
+    meets the closed triangle ABC, as a Fraction; None if it misses.  Written
+    from the same plane-parameter / barycentric formulation as
+    frac_seg_hits_tri: a crossing is at l = n.(A-P)/n.d; for a segment in the
+    plane the parameters inside the triangle form an interval whose lower end
+    is 0 or an edge-line crossing, so the smallest inside candidate is it."""
+    if not frac_seg_hits_tri(P, Q, A, B, C):
+        return None
+    d = _sub(Q, P)
+    n = _cross(_sub(B, A), _sub(C, A))
+    den = _dot(n, d)
+    if den != 0:
+        return Fraction(_dot(n, _sub(A, P)), den)
+    crit = {Fraction(0), Fraction(1)}
+    ax = max(range(3), key=lambda k: abs(n[k]))
+    keep = [k for k in range(3) if k != ax]
+    T = [A, B, C]
+    for e in range(3):
+        a, b = T[e], T[(e + 1) % 3]
+        ex, ey = b[keep[0]] - a[keep[0]], b[keep[1]] - a[keep[1]]
+        alpha = ex * (P[keep[1]] - a[keep[1]]) - ey * (P[keep[0]] - a[keep[0]])
+        beta = ex * d[keep[1]] - ey * d[keep[0]]
+        if beta != 0:
+            lam = Fraction(-alpha, beta)
+            if 0 <= lam <= 1:
+                crit.add(lam)
+    for lam in sorted(crit):
+        X = [P[k] + lam * d[k] for k in range(3)]
+        if _bary_inside(X, A, B, C, n):
+            return lam
+    return None
+
+
+def frac_first_blocker(facets, scale, P, Q):
+    """Index of the facet with the smallest first-hit parameter (ties to the
+    lower index), each facet split into its two triangles; -1 if none."""
+    P = [int(x) for x in P]
+    Q = [int(x) for x in Q]
+    best, bl = -1, None
+    for k, f in enumerate(facets):
+        o = [scale * int(f[i]) for i in range(3)]
+        u = [scale * int(f[3 + i]) for i in range(3)]
+        v = [scale * int(f[6 + i]) for i in range(3)]
+        a = o
+        b = [o[i] + u[i] for i in range(3)]
+        c = [o[i] + u[i] + v[i] for i in range(3)]
+        e = [o[i] + v[i] for i in range(3)]
+        for tri in ((a, b, c), (a, c, e)):
+            lam = frac_first_hit(P, Q, *tri)
+            if lam is not None and (bl is None or lam < bl):
+                best, bl = k, lam
+    return best

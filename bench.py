@@ -364,6 +364,33 @@ def run_ours(args, ws, rank, local):
     def per_seg(st, key):
         return st[key] / st["segments"] if st["segments"] else None
 
+    # visibility ranges, Blockage column and coherence time of this step's
+    # table (Sec. III-C/D), one call after the step, timed on its own
+    step("fast", facets_d, tx_d, rx_d, M_d, T_d, L_d, summ_d)
+    torch.cuda.synchronize()
+    rng_ms = []
+    for it in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        recs, rsum = ivm.ivm_visibility_ranges(ctx, facets_d, s, tx_d[snap_a:snap_b],
+                                               rx_d[snap_a:snap_b], T_d[snap_a:snap_b])
+        if it >= args.warmup:
+            rng_ms.append(1e3 * (time.perf_counter() - t0))
+    dt_ms = 1.0   # snapshots are 1 ms apart (120 km/h, 10/3 cm per step)
+    tc = [dt_ms * rsum["snapshots"][x] / rsum["ranges"][x] if rsum["ranges"][x] else None
+          for x in range(2)]
+    ranges_out = {
+        "what": "visibility ranges (maximal runs of each table bit), first blocker at both ends "
+                "of each, coherence time per Eq. (8)-(9); C-ABI call ivm_visibility_ranges on "
+                "this step's table, records copied to host",
+        "ms_per_call": statistics.median(rng_ms),
+        "ranges": int(len(recs)),
+        "ranges_per_side": rsum["ranges"],
+        "snapshots_per_side": rsum["snapshots"],
+        "coherence_time_ms": {"tx": tc[0], "rx": tc[1],
+                              "scenario": min(x for x in tc if x is not None) if any(tc) else None},
+        "table_bits_per_s": 2 * N * (snap_b - snap_a) / (statistics.median(rng_ms) / 1e3),
+    }
+
     value = units / (ms_fast / 1e3)
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -398,6 +425,7 @@ def run_ours(args, ws, rank, local):
             "train": {"scenes": "tiny (41 facets) + degenerate district (1,001 facets)",
                       "epochs": 12, "final_loss": train_loss, "seconds": train_s}},
         "ms_per_call": {"fast": calls_fast, "plain": calls_plain, "learned": calls_lrn},
+        "visibility_ranges": ranges_out,
         "forms_bit_identical": forms_agree,
         "gpu_launches": launches,
         "clocks": clk,

@@ -183,6 +183,47 @@ int ivm_expand_image_tree(ivm_ctx *ctx, const uint32_t *matrix, const uint32_t *
                           int32_t max_order, ivm_tree_summary *summary, int32_t *paths,
                           int64_t path_capacity, int64_t *n_paths_out);
 
+/* ------------------------------------------------------- visibility ranges
+ * Sec. III-C, Tables III-IV: along the route, a visibility range of facet j
+ * seen from a side's source (the transmitter, side 0, or the receiver, side
+ * 1) is a maximal run of consecutive snapshots [begin, end) in which bit j of
+ * that side's table row is set; begin and end are the ray creation and
+ * suppression points.  The Blockage column: at snapshot begin - 1 and at
+ * snapshot end, the first facet (smallest segment parameter, ties to the
+ * lower facet index) on the segment from the source to facet j's centre
+ * sample (a = b = floor(s / 2)); -1 where the route starts or ends, -2 where
+ * facet j does not face the source there, -3 when no facet blocks it (only
+ * for a table that does not match the geometry).  The facet's building, the
+ * paper's column, is its ivm_facet.building. */
+typedef struct ivm_range {
+    int32_t side;             /* 0: Tx row, 1: Rx row */
+    int32_t facet;            /* the visible node j */
+    int64_t begin, end;       /* snapshots [begin, end) */
+    int32_t block_before;     /* first facet on the segment at begin - 1 (or -1/-2/-3) */
+    int32_t block_after;      /* the same at end */
+} ivm_range;
+
+/* Sec. III-D, Eq. (8)-(9): with snapshots dt apart, range l lasts
+ * T_c,l = d_l / v_l = (end - begin) dt, and the mean over a side's L ranges is
+ * T_c = dt snapshots[side] / ranges[side]; with both ends moving, the smaller
+ * of the two sides' values is the scenario's. */
+typedef struct ivm_range_summary {
+    int64_t ranges[2];        /* number of ranges per side */
+    int64_t snapshots[2];     /* summed range lengths per side (= set bits) */
+} ivm_range_summary;
+
+/* Visibility ranges of one scene's table [n_snap][2][W] (as written by
+ * ivm_build_table for the same scene, params and positions tx, rx [n_snap][3]
+ * cm; host or device pointers).  ranges (host or device) receives the records
+ * ordered by side, facet, begin; *n_ranges the count.  ranges NULL: count
+ * and summary only.  Errors: IVM_ERR_ARG, IVM_ERR_RANGE (a position out of
+ * range), IVM_ERR_CAPACITY (capacity < *n_ranges; nothing written but the
+ * count and summary), IVM_ERR_TIMEOUT, IVM_ERR_CUDA. */
+int ivm_visibility_ranges(ivm_ctx *ctx, const ivm_scene *scene, const ivm_params *params,
+                          const int32_t *tx, const int32_t *rx, int64_t n_snap,
+                          const uint32_t *table, ivm_range *ranges, int64_t capacity,
+                          int64_t *n_ranges, ivm_range_summary *summary);
+
 /* ------------------------------------------------------------ learned form
  * Not in the paper: a small MLP proposes, for each candidate facet pair, the
  * order in which to walk the scene's 64 BVH clusters (64 contiguous ranges

@@ -334,7 +334,8 @@ def visibility_ranges(facets, s, tx, rx, tab, n_facets=None, threads=None):
         X = pos[side][t]
         if not _front(F, s, X, j):
             return -2
-        return first_blocker(F, s, X, j)   # >= 0: a hidden facing facet is blocked
+        f = first_blocker(F, s, X, j)
+        return f if f >= 0 else -3   # -3 only for a table that does not match the geometry
 
     def fill(k):
         r = out[k]

@@ -17,6 +17,7 @@
 
 #include "ivm_internal.cuh"
 #include "ranker.cuh"
+#include "ranges.cuh"
 #include "tree.cuh"
 
 using namespace ivm;
@@ -33,6 +34,7 @@ enum Slot {
     S_T_MAT, S_T_TAB, S_T_LOS, S_T_SUM, S_T_DEG, S_T_ROW, S_T_COL, S_T_WT, S_T_XA, S_T_XB,
     S_T_CNT, S_T_OFF, S_T_BS, S_T_BO, S_T_PATHS, S_T_FLAG, S_T_EXCL, S_T_RUN, S_T_START,
     S_TUNE_M, S_TUNE_T, S_TUNE_L,
+    S_RNG_CNT, S_RNG_OFF, S_RNG_BS, S_RNG_BO, S_RNG_SUM, S_RNG_REC, S_RNG_TAB,
     S_CBOX, S_NCL, S_RANKS, S_RFEAT, S_RLAB, S_RIDX, S_RXB, S_RYB, S_RACT, S_RLOSS, S_RWT, S_RGT,
     S_COUNT
 };
@@ -747,6 +749,97 @@ extern "C" int ivm_build_table(ivm_ctx *c, const ivm_scene *scenes, int32_t n_sc
     unsigned long long pairs = 0;
     for (int k = 0; k < n_scenes; k++) pairs += 2ull * hd[k].n * (unsigned long long)n_snap[k];
     return fill_stats(c, stats, pairs, 2);
+}
+
+extern "C" int ivm_visibility_ranges(ivm_ctx *c, const ivm_scene *scene, const ivm_params *params,
+                                     const int32_t *tx, const int32_t *rx, int64_t n_snap,
+                                     const uint32_t *table, ivm_range *ranges, int64_t capacity,
+                                     int64_t *n_ranges, ivm_range_summary *summary)
+{
+    if (!c || !scene || !n_ranges || n_snap < 0 || capacity < 0) return IVM_ERR_ARG;
+    if (n_snap > 0 && (!tx || !rx || !table)) return IVM_ERR_ARG;
+    int r = check_params(params);
+    if (r) return r;
+    DeviceGuard dg(c->device);
+    DevScenes g;
+    std::vector<SceneDesc> hd;
+    if ((r = plan_geometry(c, scene, 1, params->samples_per_side, g, hd))) return r;
+    const int n = hd[0].n, W = hd[0].W;
+    const long long S = n_snap;
+    const int nchunks = (int)((S + kRngChunk - 1) / kRngChunk);
+    const long long items = 2LL * n * nchunks;
+    const bool tab_host = S > 0 && !is_device(table);
+    const bool tx_host = S > 0 && !is_device(tx), rx_host = S > 0 && !is_device(rx);
+    const long long nb = (items + 255) / 256;
+    if ((r = ensure(c, S_RNG_CNT, sizeof(long long) * (size_t)(items + 1)))) return r;
+    if ((r = ensure(c, S_RNG_OFF, sizeof(long long) * (size_t)(items + 1)))) return r;
+    if ((r = ensure(c, S_RNG_BS, sizeof(long long) * (size_t)(nb + 1)))) return r;
+    if ((r = ensure(c, S_RNG_BO, sizeof(long long) * (size_t)(nb + 1)))) return r;
+    if ((r = ensure(c, S_RNG_SUM, sizeof(unsigned long long) * 2))) return r;
+    if ((r = ensure(c, S_RNG_TAB, tab_host ? sizeof(uint32_t) * (size_t)S * 2 * W : 0))) return r;
+    if ((r = ensure(c, S_TX, tx_host ? sizeof(int) * 3 * (size_t)S : 0))) return r;
+    if ((r = ensure(c, S_RX, rx_host ? sizeof(int) * 3 * (size_t)S : 0))) return r;
+    bind_geometry(c, g);
+    RangeArgs a;
+    a.table = tab_host ? ptr<uint32_t>(c, S_RNG_TAB) : table;
+    a.n = n;
+    a.W = W;
+    a.S = S;
+    a.nchunks = nchunks;
+    a.tx = tx_host ? ptr<int>(c, S_TX) : tx;
+    a.rx = rx_host ? ptr<int>(c, S_RX) : rx;
+    a.count = ptr<long long>(c, S_RNG_CNT);
+    a.off = ptr<long long>(c, S_RNG_OFF);
+    a.rec = nullptr;
+    a.sums = ptr<unsigned long long>(c, S_RNG_SUM);
+    if (tab_host)
+        CK(cudaMemcpyAsync(ptr<uint32_t>(c, S_RNG_TAB), table, sizeof(uint32_t) * (size_t)S * 2 * W,
+                           cudaMemcpyHostToDevice, c->stream));
+    if (tx_host)
+        CK(cudaMemcpyAsync(ptr<int>(c, S_TX), tx, sizeof(int) * 3 * (size_t)S,
+                           cudaMemcpyHostToDevice, c->stream));
+    if (rx_host)
+        CK(cudaMemcpyAsync(ptr<int>(c, S_RX), rx, sizeof(int) * 3 * (size_t)S,
+                           cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemsetAsync(a.sums, 0, sizeof(unsigned long long) * 2, c->stream));
+    long long R = 0, side0 = 0;
+    unsigned long long sums[2] = {0, 0};
+    if (items > 0) {
+        CK(ranges_count(a, c->stream));
+        CK(tree_scan(a.count, items, ptr<long long>(c, S_RNG_BS), ptr<long long>(c, S_RNG_BO),
+                     a.off, c->stream));
+        CK(cudaMemcpyAsync(&c->h_misc[0], a.off + items, sizeof(long long), cudaMemcpyDeviceToHost,
+                           c->stream));
+        CK(cudaMemcpyAsync(&c->h_misc[1], a.off + (long long)n * nchunks, sizeof(long long),
+                           cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaMemcpyAsync(sums, a.sums, sizeof(sums), cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        R = (long long)c->h_misc[0];
+        side0 = (long long)c->h_misc[1];
+    }
+    *n_ranges = R;
+    if (summary) {
+        summary->ranges[0] = side0;
+        summary->ranges[1] = R - side0;
+        summary->snapshots[0] = (int64_t)sums[0];
+        summary->snapshots[1] = (int64_t)sums[1];
+    }
+    if (!ranges || R == 0) return IVM_OK;
+    if (R > capacity) return IVM_ERR_CAPACITY;
+    const bool rec_host = !is_device(ranges);
+    if ((r = ensure(c, S_RNG_REC, rec_host ? sizeof(ivm_range) * (size_t)R : 0))) return r;
+    bind_geometry(c, g);
+    a.rec = rec_host ? ptr<ivm_range>(c, S_RNG_REC) : ranges;
+    // the scene's BVH for the Blockage walks
+    if ((r = enqueue_geometry(c, g, scene, hd, hd.data(), true))) return r;
+    CK(ranges_write(a, c->stream));
+    CK(ranges_blockers(g, a, R, c->d_err, c->stream));
+    if ((r = read_error(c))) return r;
+    if (rec_host)
+        CK(cudaMemcpyAsync(ranges, a.rec, sizeof(ivm_range) * (size_t)R, cudaMemcpyDeviceToHost,
+                           c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return IVM_OK;
 }
 
 extern "C" int ivm_expand_image_tree(ivm_ctx *c, const uint32_t *matrix, const uint32_t *table,

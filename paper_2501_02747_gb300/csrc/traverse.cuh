@@ -93,9 +93,12 @@ __device__ __forceinline__ int orient_sign(int ax, int ay, int az, int bx, int b
 // facet iff lo <= hi, lo < 1 and hi > 0.
 // (Arguments by value: the segment and the facet stay in registers in the
 // caller; only this rare path pays for the call.)
-static __device__ __noinline__ bool coplanar_hit_v(int px, int py, int pz, int dx, int dy, int dz,
-                                                   int ox, int oy, int oz, int ux, int uy, int uz,
-                                                   int vx, int vy, int vz, int dom)
+// Also gives the clip interval's lower end lo = lon / lod (lod > 0, lo >= 0):
+// the first parameter at which the segment is inside the facet.
+static __device__ __noinline__ bool coplanar_clip_v(int px, int py, int pz, int dx, int dy, int dz,
+                                                    int ox, int oy, int oz, int ux, int uy, int uz,
+                                                    int vx, int vy, int vz, int dom,
+                                                    long long *lo_num, long long *lo_den)
 {
     int a0 = dom == 0 ? 1 : 0;
     int a1 = dom == 2 ? 1 : 2;
@@ -122,7 +125,18 @@ static __device__ __noinline__ bool coplanar_hit_v(int px, int py, int pz, int d
             return false;
         }
     }
+    *lo_num = lon;
+    *lo_den = lod;
     return ((__int128)lon * hid <= (__int128)hin * lod) && (lon < lod) && (hin > 0);
+}
+
+static __device__ __noinline__ bool coplanar_hit_v(int px, int py, int pz, int dx, int dy, int dz,
+                                                   int ox, int oy, int oz, int ux, int uy, int uz,
+                                                   int vx, int vy, int vz, int dom)
+{
+    long long n, d;
+    return coplanar_clip_v(px, py, pz, dx, dy, dz, ox, oy, oz, ux, uy, uz, vx, vy, vz, dom, &n,
+                           &d);
 }
 
 __device__ __forceinline__ bool coplanar_hit(const Seg &s, const Leaf &L)

@@ -55,6 +55,22 @@ class ivm_tree_summary(ctypes.Structure):
     _fields_ = [("count", ctypes.c_uint64), ("fp0", ctypes.c_uint64), ("fp1", ctypes.c_uint64)]
 
 
+class ivm_range(ctypes.Structure):
+    _fields_ = [("side", ctypes.c_int32), ("facet", ctypes.c_int32), ("begin", ctypes.c_int64),
+                ("end", ctypes.c_int64), ("block_before", ctypes.c_int32),
+                ("block_after", ctypes.c_int32)]
+
+
+class ivm_range_summary(ctypes.Structure):
+    _fields_ = [("ranges", ctypes.c_int64 * 2), ("snapshots", ctypes.c_int64 * 2)]
+
+
+# numpy view of an ivm_range array
+RANGE_DTYPE = np.dtype({"names": ["side", "facet", "begin", "end", "block_before", "block_after"],
+                        "formats": ["<i4", "<i4", "<i8", "<i8", "<i4", "<i4"],
+                        "offsets": [0, 4, 8, 16, 24, 28], "itemsize": 32})
+
+
 _VP = ctypes.c_void_p
 _lib = None
 
@@ -69,6 +85,10 @@ SIGNATURES = {
                                ctypes.POINTER(ivm_params), ctypes.POINTER(ctypes.c_int32),
                                ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(_VP),
                                ctypes.POINTER(ivm_stats)], ctypes.c_int),
+    "ivm_visibility_ranges": ([_VP, ctypes.POINTER(ivm_scene), ctypes.POINTER(ivm_params), _VP,
+                               _VP, ctypes.c_int64, _VP, _VP, ctypes.c_int64,
+                               ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ivm_range_summary)],
+                              ctypes.c_int),
     "ivm_build_table": ([_VP, ctypes.POINTER(ivm_scene), ctypes.c_int32,
                          ctypes.POINTER(ivm_params), ctypes.POINTER(_VP), ctypes.POINTER(_VP),
                          ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(_VP),
@@ -340,6 +360,40 @@ def ivm_build_matrix_rows(ctx, facets, s, rows, mode=IVM_MODE_EXACT, flags=0, ti
     _check(lib().ivm_build_matrix_rows(ctx.handle, scenes, len(flist), ctypes.byref(p), begin,
                                        end, ptrs, ctypes.byref(st)), "ivm_build_matrix_rows")
     return (out[0] if single else out), st
+
+
+def ivm_visibility_ranges(ctx, facets, s, tx, rx, table, count_only=False):
+    """Visibility ranges of one scene's table (Sec. III-C, Tables III-IV).
+
+    facets, tx, rx, table: numpy arrays or torch tensors (host or device).
+    Returns (records: numpy RANGE_DTYPE [n], summary: dict with per-side
+    "ranges" and "snapshots" counts); with count_only, records is None."""
+    def addr(x, dtype):
+        if hasattr(x, "data_ptr"):
+            return x, x.data_ptr()
+        a = np.ascontiguousarray(x, dtype=dtype)
+        return a, a.ctypes.data
+
+    scenes, keep = _scenes([facets])
+    tx_k, tx_p = addr(tx, np.int32)
+    rx_k, rx_p = addr(rx, np.int32)
+    tb_k, tb_p = addr(table, np.uint32)
+    S = int(tx_k.shape[0])
+    p = _params(s)
+    n = ctypes.c_int64(0)
+    summ = ivm_range_summary()
+    _check(lib().ivm_visibility_ranges(ctx.handle, scenes, ctypes.byref(p), tx_p, rx_p, S, tb_p,
+                                       None, 0, ctypes.byref(n), ctypes.byref(summ)),
+           "ivm_visibility_ranges")
+    out = {"ranges": list(summ.ranges), "snapshots": list(summ.snapshots)}
+    if count_only:
+        return None, out
+    recs = np.zeros(n.value, dtype=RANGE_DTYPE)
+    if n.value:
+        _check(lib().ivm_visibility_ranges(ctx.handle, scenes, ctypes.byref(p), tx_p, rx_p, S,
+                                           tb_p, recs.ctypes.data, n.value, ctypes.byref(n),
+                                           ctypes.byref(summ)), "ivm_visibility_ranges")
+    return recs, out
 
 
 def ivm_build_table(ctx, facets, s, tx, rx, mode=IVM_MODE_EXACT, flags=0, tile=0,

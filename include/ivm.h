@@ -183,6 +183,13 @@ int ivm_expand_image_tree(ivm_ctx *ctx, const uint32_t *matrix, const uint32_t *
                           int32_t max_order, ivm_tree_summary *summary, int32_t *paths,
                           int64_t path_capacity, int64_t *n_paths_out);
 
+/* Cap on the steps of every BVH walk of this context's later calls (0: the
+ * automatic 4 N + 16, more than any valid tree needs).  A walk that runs out
+ * stops, the call returns IVM_ERR_TIMEOUT, and the context stays usable: the
+ * device-side watchdog every traversal carries, made testable.
+ * Errors: IVM_ERR_ARG (steps < 0). */
+int ivm_set_walk_budget(ivm_ctx *ctx, int32_t steps);
+
 /* ------------------------------------------------------- visibility ranges
  * Sec. III-C, Tables III-IV: along the route, a visibility range of facet j
  * seen from a side's source (the transmitter, side 0, or the receiver, side

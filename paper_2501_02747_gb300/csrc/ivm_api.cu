@@ -79,6 +79,7 @@ struct ivm_ctx {
     float *r_master = nullptr, *r_m = nullptr, *r_v = nullptr, *r_grads = nullptr;
     __nv_bfloat16 *r_wt = nullptr;
     bool has_ranker = false;
+    int walk_budget = 0;   // 0: automatic (see ivm_set_walk_budget)
 };
 
 namespace {
@@ -184,6 +185,8 @@ int plan_geometry(ivm_ctx *c, const ivm_scene *scenes, int n_scenes, int s, DevS
         D.rw0 = rw;
         D.row_lo = 0;
         D.row_hi = S.n_facets;
+        D.budget = 4 * S.n_facets + 16;   // a walk visits at most 2n - 1 nodes and leaves
+        if (c->walk_budget > 0 && c->walk_budget < D.budget) D.budget = c->walk_budget;
         facets += S.n_facets;
         nodes += S.n_facets - 1;
         samples += (long long)S.n_facets * s * s;
@@ -576,6 +579,7 @@ int build_matrix(ivm_ctx *c, const ivm_scene *scenes, int32_t n_scenes, const iv
         std::vector<unsigned long long> key = {0ull, (unsigned long long)n_scenes,
                                                (unsigned long long)learned};
         key_params(key, params);
+        key.push_back((unsigned long long)c->walk_budget);
         for (int k = 0; k < n_scenes; k++) {
             key.push_back((unsigned long long)(uintptr_t)scenes[k].facets);
             key.push_back((unsigned long long)scenes[k].n_facets);
@@ -717,6 +721,7 @@ extern "C" int ivm_build_table(ivm_ctx *c, const ivm_scene *scenes, int32_t n_sc
     if (use_graph) {
         std::vector<unsigned long long> key = {1ull, (unsigned long long)n_scenes};
         key_params(key, params);
+        key.push_back((unsigned long long)c->walk_budget);
         for (int k = 0; k < n_scenes; k++) {
             key.push_back((unsigned long long)(uintptr_t)scenes[k].facets);
             key.push_back((unsigned long long)scenes[k].n_facets);
@@ -749,6 +754,13 @@ extern "C" int ivm_build_table(ivm_ctx *c, const ivm_scene *scenes, int32_t n_sc
     unsigned long long pairs = 0;
     for (int k = 0; k < n_scenes; k++) pairs += 2ull * hd[k].n * (unsigned long long)n_snap[k];
     return fill_stats(c, stats, pairs, 2);
+}
+
+extern "C" int ivm_set_walk_budget(ivm_ctx *c, int32_t steps)
+{
+    if (!c || steps < 0) return IVM_ERR_ARG;
+    c->walk_budget = steps;
+    return IVM_OK;
 }
 
 extern "C" int ivm_visibility_ranges(ivm_ctx *c, const ivm_scene *scene, const ivm_params *params,

@@ -61,6 +61,7 @@ struct SceneDesc {
     long long nsnap;
     int row_lo;       // matrix: only pairs (i, j), i < j, with row_lo <= i < row_hi
     int row_hi;
+    int budget;       // steps of one BVH walk before IVM_ERR_TIMEOUT (>= 2n - 1 suffices)
 };
 
 // Device counters (u64), summed into ivm_stats.

@@ -124,6 +124,7 @@ extern "C" int ivm_build_matrix_noalloc(const ivm_facet *facets, int32_t n_facet
     hd.matrix = matrix;
     hd.row_lo = 0;
     hd.row_hi = n_facets;
+    hd.budget = 4 * n_facets + 16;
 
     DevScenes g = {};
     g.n_scenes = 1;

@@ -120,7 +120,7 @@ __device__ __forceinline__ void decide_pair(const DevScenes &g, int gi, int gj,
     const float dirx = (float)(2 * (Lj.ox - Li.ox) + Lj.ux + Lj.vx - Li.ux - Li.vx);
     const float diry = (float)(2 * (Lj.oy - Li.oy) + Lj.uy + Lj.vy - Li.uy - Li.vy);
     const float dirz = (float)(2 * (Lj.oz - Li.oz) + Lj.uz + Lj.vz - Li.uz - Li.vz);
-    const int budget = 4 * D.n + 16;
+    const int budget = D.budget;
     if (CACHE && kMatrixCornerProof && cache.f[0] >= 0 &&
         corners_blocked(g, baseI, baseJ, s, cache.f[0], cache.f[1], cache.f[2], cache.f[3], wc,
                         leaf))

@@ -194,7 +194,7 @@ __global__ void k_rng_blockers(DevScenes g, RangeArgs a, long long R, int *err)
         int best = -1;
         WalkCounters wc;
         int blocker, myblk = -1;
-        walk_packet(sg, alive, g.nodes, g.leaf, D.root, dx, dy, dz, 4 * D.n + 16, err, wc,
+        walk_packet(sg, alive, g.nodes, g.leaf, D.root, dx, dy, dz, D.budget, err, wc,
                     FirstHit{&ln, &ld, &best, g.order + D.facet0}, blocker, myblk);
         if (walk) result = best >= 0 ? best - D.facet0 : -3;   // -3: a facing hidden facet is blocked
     }

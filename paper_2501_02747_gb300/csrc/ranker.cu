@@ -421,7 +421,7 @@ __global__ void k_log_hits(DevScenes g, const int2 *pairs, unsigned long long np
         int blocker, myblk = -1;
         NearestHit nh{&best_t, &best_pos};
         walk_packet(sg, 1u, g.nodes, g.leaf, D.root, (float)sg.dx, (float)sg.dy, (float)sg.dz,
-                    4 * D.n + 16, err, wc, nh, blocker, myblk);
+                    D.budget, err, wc, nh, blocker, myblk);
     }
     if (lane == 0) label[w] = best_pos >= 0 ? cluster_at(C + kRCStart, best_pos) : -1;
 }

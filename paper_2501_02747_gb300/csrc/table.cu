@@ -115,7 +115,7 @@ __device__ __forceinline__ unsigned table_packet(const DevScenes &g, const Scene
     const float dirx = (float)(2 * Lf.ox + Lf.ux + Lf.vx - 2 * x);
     const float diry = (float)(2 * Lf.oy + Lf.uy + Lf.vy - 2 * y);
     const float dirz = (float)(2 * Lf.oz + Lf.uz + Lf.vz - 2 * z);
-    const int budget = 4 * D.n + 16;
+    const int budget = D.budget;
     unsigned shown = 0;   // probe lanes found free
     if (CACHE) {
         bool hit = false;
@@ -295,7 +295,7 @@ __device__ __noinline__ unsigned tile_shown(const DevScenes &g, const SceneDesc 
                         (float)-min(gx, 0), (float)-min(gy, 0), (float)-min(gz, 0)};
     int blocker, myblk = -1;
     wc.segments += cand;
-    return walk_packet(sg, pm, g.nodes, g.leaf, D.root, dirx, diry, dirz, 4 * D.n + 16, err, wc,
+    return walk_packet(sg, pm, g.nodes, g.leaf, D.root, dirx, diry, dirz, D.budget, err, wc,
                        SweepLeaf{ex, ey, ez}, blocker, myblk, f);
 }
 
@@ -417,7 +417,7 @@ __device__ __forceinline__ void table_tile(const DevScenes &g, long long item, i
                     const float dirz = (float)__shfl_sync(kFull, sg.dz, lead);
                     int myblk = -1;
                     const unsigned freem = pm & occlude<CACHE, LeafFn, false>(
-                        sg, pm, g.nodes, g.leaf, D.root, dirx, diry, dirz, 4 * D.n + 16, err, wc,
+                        sg, pm, g.nodes, g.leaf, D.root, dirx, diry, dirz, D.budget, err, wc,
                         leaf, cache, myblk);
                     word |= freem;
                     fm &= ~freem;
@@ -541,7 +541,7 @@ __device__ __forceinline__ void los_item(const DevScenes &g, long long chunk, in
     const float dirz = (float)__shfl_sync(kFull, sg.dz, lead);
     int myblk = -1;
     if (alive)
-        alive = occlude<CACHE>(sg, alive, g.nodes, g.leaf, D.root, dirx, diry, dirz, 4 * D.n + 16,
+        alive = occlude<CACHE>(sg, alive, g.nodes, g.leaf, D.root, dirx, diry, dirz, D.budget,
                                err, wc, leaf, cache, myblk);
     if (valid) D.los[t] = (uint8_t)((ok && same) || ((alive >> lane) & 1u));
 }

@@ -85,6 +85,7 @@ SIGNATURES = {
                                ctypes.POINTER(ivm_params), ctypes.POINTER(ctypes.c_int32),
                                ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(_VP),
                                ctypes.POINTER(ivm_stats)], ctypes.c_int),
+    "ivm_set_walk_budget": ([_VP, ctypes.c_int32], ctypes.c_int),
     "ivm_visibility_ranges": ([_VP, ctypes.POINTER(ivm_scene), ctypes.POINTER(ivm_params), _VP,
                                _VP, ctypes.c_int64, _VP, _VP, ctypes.c_int64,
                                ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ivm_range_summary)],
@@ -360,6 +361,11 @@ def ivm_build_matrix_rows(ctx, facets, s, rows, mode=IVM_MODE_EXACT, flags=0, ti
     _check(lib().ivm_build_matrix_rows(ctx.handle, scenes, len(flist), ctypes.byref(p), begin,
                                        end, ptrs, ctypes.byref(st)), "ivm_build_matrix_rows")
     return (out[0] if single else out), st
+
+
+def ivm_set_walk_budget(ctx, steps):
+    """Cap every BVH walk of later calls at `steps` (0: automatic)."""
+    _check(lib().ivm_set_walk_budget(ctx.handle, int(steps)), "ivm_set_walk_budget")
 
 
 def ivm_visibility_ranges(ctx, facets, s, tx, rx, table, count_only=False):

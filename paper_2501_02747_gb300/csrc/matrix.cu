@@ -166,8 +166,14 @@ __device__ __forceinline__ void decide_pair(const DevScenes &g, int gi, int gj,
     }
 }
 
+// Register cap of the matrix kernel: 8 resident blocks of 128 threads (64
+// registers; a sweep of 3-12 blocks on the district and the city: more warps
+// hide the dependent box-test latency better than the spills cost).  The
+// learned walk holds more state and keeps 4.
+constexpr int kMatrixMinBlocks = 8, kMatrixMinBlocksLearned = 4;
+
 template <bool PERSIST, bool CACHE, bool LEARN, class LeafFn>
-__global__ void __launch_bounds__(kTravThreads, IVM_MIN_BLOCKS)
+__global__ void __launch_bounds__(kTravThreads, LEARN ? kMatrixMinBlocksLearned : kMatrixMinBlocks)
 k_matrix(DevScenes g, const int2 *pairs, unsigned long long npairs, int tile,
          const unsigned long long *count_dev, LearnedDev lrn, unsigned long long *work,
          unsigned long long *ctr, int *err)

@@ -547,8 +547,12 @@ __device__ __forceinline__ void los_item(const DevScenes &g, long long chunk, in
 }
 
 // Items [0, total_items) are table tiles; the next total_los_chunks are LoS.
+// Register cap of the table kernel: 8 resident blocks of 128 threads (a
+// sweep of 3-8 on the district).
+constexpr int kTableMinBlocks = 8;
+
 template <bool PERSIST, bool CACHE, class LeafFn>
-__global__ void __launch_bounds__(kTravThreads, IVM_MIN_BLOCKS)
+__global__ void __launch_bounds__(kTravThreads, kTableMinBlocks)
 k_table(DevScenes g, long long total_items, long long all_items, int TT,
                         const int *rep, unsigned long long *work, unsigned long long *ctr,
                         int *err)

@@ -391,6 +391,33 @@ def run_ours(args, ws, rank, local):
         "table_bits_per_s": 2 * N * (snap_b - snap_a) / (statistics.median(rng_ms) / 1e3),
     }
 
+    # image-method validation of the step's image-tree candidates (Sec. IV-B),
+    # orders 0..2 at the first snapshots of this rank's range, timed on its own
+    ray_snaps, ray_K = min(4, snap_b - snap_a), 2
+    a0, a1 = snap_a, snap_a + ray_snaps
+    _, n_cand = ivm.ivm_expand_image_tree(ctx, M_d, T_d[a0:a1], L_d[a0:a1], N, ray_K,
+                                          count_paths=True)
+    _, cand, n_cand, _ = ivm.ivm_expand_image_tree(ctx, M_d, T_d[a0:a1], L_d[a0:a1], N, ray_K,
+                                                   paths_capacity=max(n_cand, 1))
+    cand = cand[:n_cand]
+    flags = torch.zeros(max(n_cand, 1), dtype=torch.uint8, device=dev)
+    ray_ms = []
+    for it in range(args.warmup + args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ivm.ivm_validate_paths(ctx, facets_d, s, tx_d[a0:a1], rx_d[a0:a1], cand, ray_K,
+                               out=flags[:n_cand])
+        if it >= args.warmup:
+            ray_ms.append(1e3 * (time.perf_counter() - t0))
+    n_valid = int(flags[:n_cand].sum().item()) if n_cand else 0
+    rays_out = {
+        "what": "image-method validation of image-tree candidates (orders 0-2) as specular "
+                f"rays, C-ABI call ivm_validate_paths, snapshots {a0}..{a1 - 1}",
+        "candidates": int(n_cand), "valid_rays": n_valid,
+        "ms_per_call": statistics.median(ray_ms),
+        "candidates_per_s": n_cand / (statistics.median(ray_ms) / 1e3) if ray_ms else None,
+    }
+
     value = units / (ms_fast / 1e3)
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -426,6 +453,7 @@ def run_ours(args, ws, rank, local):
                       "epochs": 12, "final_loss": train_loss, "seconds": train_s}},
         "ms_per_call": {"fast": calls_fast, "plain": calls_plain, "learned": calls_lrn},
         "visibility_ranges": ranges_out,
+        "ray_validation": rays_out,
         "forms_bit_identical": forms_agree,
         "gpu_launches": launches,
         "clocks": clk,

@@ -231,6 +231,27 @@ int ivm_visibility_ranges(ivm_ctx *ctx, const ivm_scene *scene, const ivm_params
                           const uint32_t *table, ivm_range *ranges, int64_t capacity,
                           int64_t *n_ranges, ivm_range_summary *summary);
 
+/* ------------------------------------------------- ray validation
+ * The image method on image-tree candidates (Sec. IV-B: the pre-processed
+ * image tree and the brute-force method give the same valid rays).  For path
+ * record (t, k, f1..fk), source T = tx[t] and receiver R = rx[t]: images I_0
+ * = T, I_m = the mirror image of I_(m-1) in the plane of f_m; reflection
+ * points from the receiver back, P_(k+1) = R and P_m where the segment from
+ * P_(m+1) to I_m crosses the plane of f_m strictly inside it; the candidate is
+ * a valid ray when every P_m lies in the closed face f_m, I_(m-1) and P_(m+1)
+ * are strictly in front of f_m, and no facet meets any open leg P_m -> P_(m+1)
+ * (P_0 = T).  Order 0 is the direct segment.  Exact integer arithmetic;
+ * every facet of the scene must be an axis-aligned rectangle.
+ *
+ * paths [n_paths][max_order + 2] as written by ivm_expand_image_tree (host or
+ * device); valid [n_paths] receives 1 or 0 (host or device); max_order <= 8.
+ * Errors: IVM_ERR_ARG (a facet not axis-aligned, a record with t or k or a
+ * facet index out of range), IVM_ERR_RANGE, IVM_ERR_TIMEOUT, IVM_ERR_CUDA. */
+int ivm_validate_paths(ivm_ctx *ctx, const ivm_scene *scene, const ivm_params *params,
+                       const int32_t *tx, const int32_t *rx, int64_t n_snap,
+                       const int32_t *paths, int64_t n_paths, int32_t max_order,
+                       uint8_t *valid);
+
 /* ------------------------------------------------------------ learned form
  * Not in the paper: a small MLP proposes, for each candidate facet pair, the
  * order in which to walk the scene's 64 BVH clusters (64 contiguous ranges

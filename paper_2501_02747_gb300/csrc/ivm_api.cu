@@ -18,6 +18,7 @@
 #include "ivm_internal.cuh"
 #include "ranker.cuh"
 #include "ranges.cuh"
+#include "rays.cuh"
 #include "tree.cuh"
 
 using namespace ivm;
@@ -34,6 +35,7 @@ enum Slot {
     S_T_MAT, S_T_TAB, S_T_LOS, S_T_SUM, S_T_DEG, S_T_ROW, S_T_COL, S_T_WT, S_T_XA, S_T_XB,
     S_T_CNT, S_T_OFF, S_T_BS, S_T_BO, S_T_PATHS, S_T_FLAG, S_T_EXCL, S_T_RUN, S_T_START,
     S_TUNE_M, S_TUNE_T, S_TUNE_L,
+    S_RAY_PATHS, S_RAY_VALID,
     S_RNG_CNT, S_RNG_OFF, S_RNG_BS, S_RNG_BO, S_RNG_SUM, S_RNG_REC, S_RNG_TAB,
     S_CBOX, S_NCL, S_RANKS, S_RFEAT, S_RLAB, S_RIDX, S_RXB, S_RYB, S_RACT, S_RLOSS, S_RWT, S_RGT,
     S_COUNT
@@ -754,6 +756,69 @@ extern "C" int ivm_build_table(ivm_ctx *c, const ivm_scene *scenes, int32_t n_sc
     unsigned long long pairs = 0;
     for (int k = 0; k < n_scenes; k++) pairs += 2ull * hd[k].n * (unsigned long long)n_snap[k];
     return fill_stats(c, stats, pairs, 2);
+}
+
+extern "C" int ivm_validate_paths(ivm_ctx *c, const ivm_scene *scene, const ivm_params *params,
+                                  const int32_t *tx, const int32_t *rx, int64_t n_snap,
+                                  const int32_t *paths, int64_t n_paths, int32_t max_order,
+                                  uint8_t *valid)
+{
+    if (!c || !scene || n_snap < 0 || n_paths < 0 || max_order < 0 || max_order > kRayMaxOrder)
+        return IVM_ERR_ARG;
+    if (n_paths > 0 && (!paths || !valid || !tx || !rx)) return IVM_ERR_ARG;
+    int r = check_params(params);
+    if (r) return r;
+    if (!scene->facets || scene->n_facets < 1) return IVM_ERR_ARG;
+    DeviceGuard dg(c->device);
+    // every facet an axis-aligned rectangle: u and v along two different axes
+    {
+        std::vector<ivm_facet> hf(scene->n_facets);
+        CK(cudaMemcpy(hf.data(), scene->facets, sizeof(ivm_facet) * hf.size(), cudaMemcpyDefault));
+        for (const ivm_facet &f : hf) {
+            int nu = 0, nv = 0, au = -1, av = -1;
+            for (int i = 0; i < 3; i++) {
+                if (f.u[i]) { nu++; au = i; }
+                if (f.v[i]) { nv++; av = i; }
+            }
+            if (nu != 1 || nv != 1 || au == av) return IVM_ERR_ARG;
+        }
+    }
+    DevScenes g;
+    std::vector<SceneDesc> hd;
+    if ((r = plan_geometry(c, scene, 1, params->samples_per_side, g, hd))) return r;
+    if (n_paths == 0) return IVM_OK;
+    const bool p_host = !is_device(paths), v_host = !is_device(valid);
+    const bool tx_host = !is_device(tx), rx_host = !is_device(rx);
+    const size_t rec = (size_t)max_order + 2;
+    if ((r = ensure(c, S_RAY_PATHS, p_host ? sizeof(int) * rec * (size_t)n_paths : 0))) return r;
+    if ((r = ensure(c, S_RAY_VALID, v_host ? (size_t)n_paths : 0))) return r;
+    if ((r = ensure(c, S_TX, tx_host ? sizeof(int) * 3 * (size_t)n_snap : 0))) return r;
+    if ((r = ensure(c, S_RX, rx_host ? sizeof(int) * 3 * (size_t)n_snap : 0))) return r;
+    bind_geometry(c, g);
+    RayArgs a;
+    a.tx = tx_host ? ptr<int>(c, S_TX) : tx;
+    a.rx = rx_host ? ptr<int>(c, S_RX) : rx;
+    a.n_snap = n_snap;
+    a.paths = p_host ? ptr<int>(c, S_RAY_PATHS) : paths;
+    a.n_paths = n_paths;
+    a.max_order = max_order;
+    a.valid = v_host ? ptr<uint8_t>(c, S_RAY_VALID) : valid;
+    if (tx_host)
+        CK(cudaMemcpyAsync(ptr<int>(c, S_TX), tx, sizeof(int) * 3 * (size_t)n_snap,
+                           cudaMemcpyHostToDevice, c->stream));
+    if (rx_host)
+        CK(cudaMemcpyAsync(ptr<int>(c, S_RX), rx, sizeof(int) * 3 * (size_t)n_snap,
+                           cudaMemcpyHostToDevice, c->stream));
+    if (p_host)
+        CK(cudaMemcpyAsync(ptr<int>(c, S_RAY_PATHS), paths, sizeof(int) * rec * (size_t)n_paths,
+                           cudaMemcpyHostToDevice, c->stream));
+    if ((r = enqueue_geometry(c, g, scene, hd, hd.data(), true))) return r;
+    CK(rays_validate(g, a, c->d_err, c->stream));
+    if ((r = read_error(c))) return r;
+    if (v_host)
+        CK(cudaMemcpyAsync(valid, a.valid, (size_t)n_paths, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return IVM_OK;
 }
 
 extern "C" int ivm_set_walk_budget(ivm_ctx *c, int32_t steps)

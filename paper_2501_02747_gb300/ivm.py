@@ -86,6 +86,9 @@ SIGNATURES = {
                                ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(_VP),
                                ctypes.POINTER(ivm_stats)], ctypes.c_int),
     "ivm_set_walk_budget": ([_VP, ctypes.c_int32], ctypes.c_int),
+    "ivm_validate_paths": ([_VP, ctypes.POINTER(ivm_scene), ctypes.POINTER(ivm_params), _VP, _VP,
+                            ctypes.c_int64, _VP, ctypes.c_int64, ctypes.c_int32, _VP],
+                           ctypes.c_int),
     "ivm_visibility_ranges": ([_VP, ctypes.POINTER(ivm_scene), ctypes.POINTER(ivm_params), _VP,
                                _VP, ctypes.c_int64, _VP, _VP, ctypes.c_int64,
                                ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ivm_range_summary)],
@@ -361,6 +364,30 @@ def ivm_build_matrix_rows(ctx, facets, s, rows, mode=IVM_MODE_EXACT, flags=0, ti
     _check(lib().ivm_build_matrix_rows(ctx.handle, scenes, len(flist), ctypes.byref(p), begin,
                                        end, ptrs, ctypes.byref(st)), "ivm_build_matrix_rows")
     return (out[0] if single else out), st
+
+
+def ivm_validate_paths(ctx, facets, s, tx, rx, paths, max_order, out=None):
+    """Valid-ray flags (uint8 [n]) of image-tree path records [n][max_order + 2]
+    (numpy or torch, host or device); returned as numpy unless `out` is given."""
+    def addr(x, dtype):
+        if hasattr(x, "data_ptr"):
+            return x, x.data_ptr()
+        arr = np.ascontiguousarray(x, dtype=dtype)
+        return arr, arr.ctypes.data
+
+    scenes, keep = _scenes([facets])
+    tx_k, tx_p = addr(tx, np.int32)
+    rx_k, rx_p = addr(rx, np.int32)
+    pa_k, pa_p = addr(paths, np.int32)
+    n = int(pa_k.shape[0]) if pa_k.ndim > 1 else 0
+    if out is None:
+        out = np.zeros(n, dtype=np.uint8)
+    _o, o_p = addr(out, np.uint8)
+    p = _params(s)
+    _check(lib().ivm_validate_paths(ctx.handle, scenes, ctypes.byref(p), tx_p, rx_p,
+                                    int(tx_k.shape[0]), pa_p, n, int(max_order), o_p),
+           "ivm_validate_paths")
+    return out
 
 
 def ivm_set_walk_budget(ctx, steps):

@@ -547,9 +547,11 @@ __device__ __forceinline__ void los_item(const DevScenes &g, long long chunk, in
 }
 
 // Items [0, total_items) are table tiles; the next total_los_chunks are LoS.
-// Register cap of the table kernel: 8 resident blocks of 128 threads (a
-// sweep of 3-8 on the district).
-constexpr int kTableMinBlocks = 8;
+// Register cap of the table kernel: 4 resident blocks of 128 threads.  A
+// sweep of 4-8 on the district gave the same times at fixed launch shapes
+// (the kernel is bound by its work items' latency, not by resident warps),
+// and 4 keeps the per-snapshot state in registers (8 spills 1.5 KB a thread).
+constexpr int kTableMinBlocks = 4;
 
 template <bool PERSIST, bool CACHE, class LeafFn>
 __global__ void __launch_bounds__(kTravThreads, kTableMinBlocks)

@@ -1365,7 +1365,7 @@ extern "C" int ivm_autotune(ivm_ctx *c, const ivm_scene *scenes, int32_t n_scene
             float ms = 1e30f;
             for (int rep = 0; rep < 3; rep++) {   // the first run warms the arena up
                 if ((r = ivm_build_matrix(c, scenes, ns, &p, mout.data(), &st))) return r;
-                if (rep > 0 && st.ms_traverse < ms) ms = st.ms_traverse;
+                if (rep == 1 || (rep > 1 && st.ms_traverse > ms)) ms = st.ms_traverse;
             }
             if (first || ms < bm) { bm = ms; mt = tile; }
             first = false;
@@ -1377,11 +1377,11 @@ extern "C" int ivm_autotune(ivm_ctx *c, const ivm_scene *scenes, int32_t n_scene
                 p.table_tile = tile;
                 ivm_stats st;
                 float ms = 1e30f;
-                for (int rep = 0; rep < 3; rep++) {   // warm-up, then the faster of two
+                for (int rep = 0; rep < 3; rep++) {   // warm-up, then the slower of two
                     if ((r = ivm_build_table(c, scenes, ns, &p, tx, rx, snaps.data(), tout.data(),
                                              lout.data(), &st)))
                         return r;
-                    if (rep > 0 && st.ms_traverse < ms) ms = st.ms_traverse;
+                    if (rep == 1 || (rep > 1 && st.ms_traverse > ms)) ms = st.ms_traverse;
                 }
                 if (first || ms < bt) { bt = ms; tt = tile; }
                 first = false;

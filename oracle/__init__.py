@@ -84,6 +84,10 @@ def lib():
         L.oracle_first_blocker.argtypes = [_i32p, ctypes.c_int32, ctypes.c_int32, _i32p,
                                            ctypes.c_int32]
         L.oracle_first_blocker.restype = ctypes.c_int32
+        L.oracle_edge_table.argtypes = [_i32p, ctypes.c_int32, ctypes.c_int32, _i32p,
+                                        ctypes.c_int32, _i32p, _i32p, ctypes.c_int64,
+                                        ctypes.c_int64, _u32p, _i32p]
+        L.oracle_edge_table.restype = None
         _lib = L
     return _lib
 
@@ -348,3 +352,28 @@ def visibility_ranges(facets, s, tx, rx, tab, n_facets=None, threads=None):
     snaps = np.array([np.sum((out["end"] - out["begin"])[out["side"] == x]) for x in range(2)],
                      dtype=np.int64)
     return out, ranges, snaps
+
+
+# ---------------------------------------------------------------- edges
+
+def edge_table(facets, s, edges, tx, rx, snaps=None, threads=None):
+    """Edge rows (step 9 of ivm_oracle.c) for the given snapshots:
+    (uint32 [n][2][WE], int32 nearest [n][2])."""
+    F = _facets(facets)
+    E = np.ascontiguousarray(edges, dtype=np.int32).reshape(-1, 6)
+    tx = np.ascontiguousarray(tx, dtype=np.int32).reshape(-1, 3)
+    rx = np.ascontiguousarray(rx, dtype=np.int32).reshape(-1, 3)
+    snaps = np.arange(tx.shape[0]) if snaps is None else np.asarray(snaps, dtype=np.int64)
+    WE = words(E.shape[0])
+    tab = np.zeros((len(snaps), 2, WE), dtype=np.uint32)
+    near = np.zeros((len(snaps), 2), dtype=np.int32)
+    L = lib()
+
+    def one(k):
+        t = int(snaps[k])
+        L.oracle_edge_table(_p(F, _i32p), F.shape[0], s, _p(E, _i32p), E.shape[0], _p(tx, _i32p),
+                            _p(rx, _i32p), t, t + 1, _p(tab[k], _u32p), _p(near[k], _i32p))
+
+    with ThreadPoolExecutor(_threads(threads)) as ex:
+        list(ex.map(one, range(len(snaps))))
+    return tab, near

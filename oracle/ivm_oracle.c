@@ -44,6 +44,13 @@
  *  7. Traditional per-snapshot method [Sec. IV-B, brute-force image tree per
  *     location]: the same path sets with every hop's visibility recomputed
  *     from geometry at every snapshot, no cached matrix.
+ *  9. Edges [Sec. I and II: the matrix lists visible faces and edges;
+ *     Sec. III-B: first-order diffraction uses the edge closest to the
+ *     receiver].  Edge e = segment A -> B (cm) has s samples at the cell
+ *     centres p_a = 2s A + (2a+1)(B - A), a in [0, s).  vis_X[t][e] = some
+ *     sample p_a has not blocked(X_t, p_a); the nearest visible edge of X_t is
+ *     the one holding the visible sample closest to X_t (squared distance,
+ *     ties to the lower edge index), -1 if none.
  *  8. Blockage [Sec. III-C, Tables III-IV, "Blockage" column]: the first
  *     facet the segment from a source point to facet j's centre sample
  *     (a = b = floor(s/2)) meets, i.e. the hit with the smallest parameter l
@@ -353,6 +360,41 @@ OR_EXPORT int32_t oracle_first_blocker(const int32_t *facets, int32_t n, int32_t
     int32_t r = first_blocker(F, n, point_of(X, s), sample(&F[j], s, s / 2, s / 2));
     free(F);
     return r;
+}
+
+/* step 9: edge rows for snapshots [t0, t1): table is (t1 - t0) x 2 x WE words
+ * (WE = ceil(ne / 32)), nearest is (t1 - t0) x 2 edge indices. */
+OR_EXPORT void oracle_edge_table(const int32_t *facets, int32_t n, int32_t s,
+                                 const int32_t *edges, int32_t ne, const int32_t *tx,
+                                 const int32_t *rx, int64_t t0, int64_t t1, uint32_t *table,
+                                 int32_t *nearest)
+{
+    int32_t WE = oracle_words(ne);
+    Facet *F = load_facets(facets, n, s);
+    memset(table, 0, sizeof(uint32_t) * (size_t)WE * 2 * (size_t)(t1 - t0));
+    for (int64_t t = t0; t < t1; t++) {
+        V X[2] = {point_of(tx + 3 * t, s), point_of(rx + 3 * t, s)};
+        for (int side = 0; side < 2; side++) {
+            uint32_t *row = table + ((size_t)(t - t0) * 2 + side) * WE;
+            int32_t best = -1;
+            i128 bd = 0;
+            for (int32_t e = 0; e < ne; e++) {
+                const int32_t *E = edges + 6 * (size_t)e;
+                V A = scl(2 * (i128)s, mk(E[0], E[1], E[2]));
+                V d = sub(mk(E[3], E[4], E[5]), mk(E[0], E[1], E[2]));
+                for (int a = 0; a < s; a++) {
+                    V p = add(A, scl(2 * a + 1, d));
+                    if (blocked(F, n, X[side], p)) continue;
+                    row[e >> 5] |= 1u << (e & 31);
+                    V r = sub(p, X[side]);
+                    i128 d2 = dot(r, r);
+                    if (best < 0 || d2 < bd) { best = e; bd = d2; }
+                }
+            }
+            nearest[(t - t0) * 2 + side] = best;
+        }
+    }
+    free(F);
 }
 
 /* Number of sample pairs (p_a on i, q_b on j) that satisfy the three

@@ -88,6 +88,25 @@ def box_facets(x0, y0, x1, y1, h, building):
     ]
 
 
+def box_edges(x0, y0, x1, y1, h):
+    """The eight convex edges of the box [x0,x1]x[y0,y1]x[0,h]: four vertical,
+    four around the roof (the edges on the ground are concave and left out)."""
+    return [
+        (x0, y0, 0, x0, y0, h), (x1, y0, 0, x1, y0, h),
+        (x1, y1, 0, x1, y1, h), (x0, y1, 0, x0, y1, h),
+        (x0, y0, h, x1, y0, h), (x1, y0, h, x1, y1, h),
+        (x1, y1, h, x0, y1, h), (x0, y1, h, x0, y0, h),
+    ]
+
+
+def edges_of(scene) -> np.ndarray:
+    """Convex edges of a scene's box buildings, int32 [E][6] (endpoints, cm)."""
+    rows = []
+    for (x0, y0, x1, y1, h) in scene.boxes:
+        rows.extend(box_edges(x0, y0, x1, y1, h))
+    return np.asarray(rows, dtype=np.int32).reshape(-1, 6)
+
+
 def ground_facet(side):
     """One facet covering the whole square, building footprints included."""
     return (0, 0, 0, side, 0, 0, 0, side, 0, -1)

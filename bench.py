@@ -410,6 +410,27 @@ def run_ours(args, ws, rank, local):
         if it >= args.warmup:
             ray_ms.append(1e3 * (time.perf_counter() - t0))
     n_valid = int(flags[:n_cand].sum().item()) if n_cand else 0
+    # edges as visible nodes and the edge nearest each source (Sec. III-B), timed on its own
+    E_d = torch.from_numpy(sg.edges_of(sc)).to(dev)
+    edge_ms = []
+    for it in range(args.warmup + args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        etab, enear = ivm.ivm_build_edge_table(ctx, facets_d, s, E_d, tx_d[snap_a:snap_b],
+                                               rx_d[snap_a:snap_b], mode=ivm.IVM_MODE_FILTERED)
+        if it >= args.warmup:
+            edge_ms.append(1e3 * (time.perf_counter() - t0))
+    ebits = np.unpackbits(etab.view(np.uint8), axis=-1, bitorder="little")[..., :E_d.shape[0]]
+    edges_out = {
+        "what": "edge rows (the 8 convex edges of every building as visible nodes, s samples "
+                "each) and the nearest visible edge per source, C-ABI call ivm_build_edge_table, "
+                "results copied to host",
+        "edges": int(E_d.shape[0]), "ms_per_call": statistics.median(edge_ms),
+        "edge_tests_per_s": 2 * int(E_d.shape[0]) * (snap_b - snap_a) /
+                            (statistics.median(edge_ms) / 1e3),
+        "visible_edges_mean": [float(ebits[:, 0].sum(axis=1).mean()),
+                               float(ebits[:, 1].sum(axis=1).mean())],
+    }
     rays_out = {
         "what": "image-method validation of image-tree candidates (orders 0-2) as specular "
                 f"rays, C-ABI call ivm_validate_paths, snapshots {a0}..{a1 - 1}",
@@ -454,6 +475,7 @@ def run_ours(args, ws, rank, local):
         "ms_per_call": {"fast": calls_fast, "plain": calls_plain, "learned": calls_lrn},
         "visibility_ranges": ranges_out,
         "ray_validation": rays_out,
+        "edges": edges_out,
         "forms_bit_identical": forms_agree,
         "gpu_launches": launches,
         "clocks": clk,

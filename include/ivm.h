@@ -231,6 +231,26 @@ int ivm_visibility_ranges(ivm_ctx *ctx, const ivm_scene *scene, const ivm_params
                           const uint32_t *table, ivm_range *ranges, int64_t capacity,
                           int64_t *n_ranges, ivm_range_summary *summary);
 
+/* ---------------------------------------------------------------- edges
+ * Edges as visible nodes (the matrix and table list visible faces and edges:
+ * Sec. I-II) and the edge nearest a source (first-order diffraction by the
+ * edge closest to the receiver: Sec. III-B).  Edge e is the segment from
+ * (edges[6e], edges[6e+1], edges[6e+2]) to (edges[6e+3..6e+5]), cm, with s
+ * samples at the cell centres A + (2a+1)/(2s) (B - A).  For each snapshot
+ * and side (0: Tx, 1: Rx), bit e of the row is 1 when some sample of e is
+ * reachable from the source by a segment no facet blocks (open segment,
+ * closed facets), and nearest holds the visible edge with the sample
+ * closest to the source (squared distance over all of its samples, ties to
+ * the lower index), -1 if none.
+ *
+ * table [n_snap][2][WE] (WE = ceil(n_edges / 32)) and nearest [n_snap][2]:
+ * host or device.  Errors: IVM_ERR_ARG (n_edges outside 0..65535),
+ * IVM_ERR_RANGE (a source or an edge sample out of range), IVM_ERR_TIMEOUT,
+ * IVM_ERR_CUDA. */
+int ivm_build_edge_table(ivm_ctx *ctx, const ivm_scene *scene, const ivm_params *params,
+                         const int32_t *edges, int32_t n_edges, const int32_t *tx,
+                         const int32_t *rx, int64_t n_snap, uint32_t *table, int32_t *nearest);
+
 /* ------------------------------------------------- ray validation
  * The image method on image-tree candidates (Sec. IV-B: the pre-processed
  * image tree and the brute-force method give the same valid rays).  For path

@@ -49,8 +49,8 @@
  *     receiver].  Edge e = segment A -> B (cm) has s samples at the cell
  *     centres p_a = 2s A + (2a+1)(B - A), a in [0, s).  vis_X[t][e] = some
  *     sample p_a has not blocked(X_t, p_a); the nearest visible edge of X_t is
- *     the one holding the visible sample closest to X_t (squared distance,
- *     ties to the lower edge index), -1 if none.
+ *     the visible edge with the sample closest to X_t (squared distance over
+ *     all of its samples, ties to the lower edge index), -1 if none.
  *  8. Blockage [Sec. III-C, Tables III-IV, "Blockage" column]: the first
  *     facet the segment from a source point to facet j's centre sample
  *     (a = b = floor(s/2)) meets, i.e. the hit with the smallest parameter l
@@ -382,14 +382,17 @@ OR_EXPORT void oracle_edge_table(const int32_t *facets, int32_t n, int32_t s,
                 const int32_t *E = edges + 6 * (size_t)e;
                 V A = scl(2 * (i128)s, mk(E[0], E[1], E[2]));
                 V d = sub(mk(E[3], E[4], E[5]), mk(E[0], E[1], E[2]));
+                int vis = 0;
+                i128 emin = 0;
                 for (int a = 0; a < s; a++) {
                     V p = add(A, scl(2 * a + 1, d));
-                    if (blocked(F, n, X[side], p)) continue;
-                    row[e >> 5] |= 1u << (e & 31);
                     V r = sub(p, X[side]);
-                    i128 d2 = dot(r, r);
-                    if (best < 0 || d2 < bd) { best = e; bd = d2; }
+                    if (a == 0 || dot(r, r) < emin) emin = dot(r, r);
+                    if (!vis && !blocked(F, n, X[side], p)) vis = 1;
                 }
+                if (!vis) continue;
+                row[e >> 5] |= 1u << (e & 31);
+                if (best < 0 || emin < bd) { best = e; bd = emin; }
             }
             nearest[(t - t0) * 2 + side] = best;
         }

@@ -17,6 +17,7 @@
 
 #include "ivm_internal.cuh"
 #include "ranker.cuh"
+#include "edges.cuh"
 #include "ranges.cuh"
 #include "rays.cuh"
 #include "tree.cuh"
@@ -35,6 +36,7 @@ enum Slot {
     S_T_MAT, S_T_TAB, S_T_LOS, S_T_SUM, S_T_DEG, S_T_ROW, S_T_COL, S_T_WT, S_T_XA, S_T_XB,
     S_T_CNT, S_T_OFF, S_T_BS, S_T_BO, S_T_PATHS, S_T_FLAG, S_T_EXCL, S_T_RUN, S_T_START,
     S_TUNE_M, S_TUNE_T, S_TUNE_L,
+    S_EDGES, S_EDGE_TAB, S_EDGE_KEY, S_EDGE_NEAR,
     S_RAY_PATHS, S_RAY_VALID,
     S_RNG_CNT, S_RNG_OFF, S_RNG_BS, S_RNG_BO, S_RNG_SUM, S_RNG_REC, S_RNG_TAB,
     S_CBOX, S_NCL, S_RANKS, S_RFEAT, S_RLAB, S_RIDX, S_RXB, S_RYB, S_RACT, S_RLOSS, S_RWT, S_RGT,
@@ -756,6 +758,70 @@ extern "C" int ivm_build_table(ivm_ctx *c, const ivm_scene *scenes, int32_t n_sc
     unsigned long long pairs = 0;
     for (int k = 0; k < n_scenes; k++) pairs += 2ull * hd[k].n * (unsigned long long)n_snap[k];
     return fill_stats(c, stats, pairs, 2);
+}
+
+extern "C" int ivm_build_edge_table(ivm_ctx *c, const ivm_scene *scene, const ivm_params *params,
+                                    const int32_t *edges, int32_t n_edges, const int32_t *tx,
+                                    const int32_t *rx, int64_t n_snap, uint32_t *table,
+                                    int32_t *nearest)
+{
+    if (!c || !scene || n_edges < 0 || n_edges > 0xffff || n_snap < 0) return IVM_ERR_ARG;
+    if (n_snap > 0 && (!tx || !rx || !table || !nearest)) return IVM_ERR_ARG;
+    if (n_edges > 0 && !edges) return IVM_ERR_ARG;
+    int r = check_params(params);
+    if (r) return r;
+    DeviceGuard dg(c->device);
+    DevScenes g;
+    std::vector<SceneDesc> hd;
+    if ((r = plan_geometry(c, scene, 1, params->samples_per_side, g, hd))) return r;
+    if (n_snap == 0) return IVM_OK;
+    const int WE = words(n_edges);
+    const size_t S = (size_t)n_snap;
+    const bool e_host = n_edges > 0 && !is_device(edges);
+    const bool tx_host = !is_device(tx), rx_host = !is_device(rx);
+    const bool t_host = !is_device(table), n_host = !is_device(nearest);
+    if ((r = ensure(c, S_EDGES, e_host ? sizeof(int) * 6 * (size_t)n_edges : 0))) return r;
+    if ((r = ensure(c, S_EDGE_TAB, t_host ? sizeof(uint32_t) * S * 2 * WE : 0))) return r;
+    if ((r = ensure(c, S_EDGE_KEY, sizeof(unsigned long long) * 2 * S))) return r;
+    if ((r = ensure(c, S_EDGE_NEAR, n_host ? sizeof(int) * 2 * S : 0))) return r;
+    if ((r = ensure(c, S_TX, tx_host ? sizeof(int) * 3 * S : 0))) return r;
+    if ((r = ensure(c, S_RX, rx_host ? sizeof(int) * 3 * S : 0))) return r;
+    bind_geometry(c, g);
+    EdgeArgs a;
+    a.edges = e_host ? ptr<int>(c, S_EDGES) : edges;
+    a.ne = n_edges;
+    a.WE = WE;
+    a.tx = tx_host ? ptr<int>(c, S_TX) : tx;
+    a.rx = rx_host ? ptr<int>(c, S_RX) : rx;
+    a.S = n_snap;
+    a.tile = params->table_tile > 0 ? params->table_tile : 32;
+    a.ntiles = (n_snap + a.tile - 1) / a.tile;
+    a.table = t_host ? ptr<uint32_t>(c, S_EDGE_TAB) : table;
+    a.nearest_key = ptr<unsigned long long>(c, S_EDGE_KEY);
+    a.nearest = n_host ? ptr<int>(c, S_EDGE_NEAR) : nearest;
+    a.ctr = c->d_ctr;
+    if (e_host)
+        CK(cudaMemcpyAsync(ptr<int>(c, S_EDGES), edges, sizeof(int) * 6 * (size_t)n_edges,
+                           cudaMemcpyHostToDevice, c->stream));
+    if (tx_host)
+        CK(cudaMemcpyAsync(ptr<int>(c, S_TX), tx, sizeof(int) * 3 * S, cudaMemcpyHostToDevice,
+                           c->stream));
+    if (rx_host)
+        CK(cudaMemcpyAsync(ptr<int>(c, S_RX), rx, sizeof(int) * 3 * S, cudaMemcpyHostToDevice,
+                           c->stream));
+    if ((r = enqueue_geometry(c, g, scene, hd, hd.data(), true))) return r;
+    if (WE > 0)
+        CK(cudaMemsetAsync(a.table, 0, sizeof(uint32_t) * S * 2 * WE, c->stream));
+    CK(edges_table(g, a, params->mode != IVM_MODE_EXACT, c->d_err, c->stream));
+    if ((r = read_error(c))) return r;
+    if (t_host && WE > 0)
+        CK(cudaMemcpyAsync(table, a.table, sizeof(uint32_t) * S * 2 * WE, cudaMemcpyDeviceToHost,
+                           c->stream));
+    if (n_host)
+        CK(cudaMemcpyAsync(nearest, a.nearest, sizeof(int) * 2 * S, cudaMemcpyDeviceToHost,
+                           c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return IVM_OK;
 }
 
 extern "C" int ivm_validate_paths(ivm_ctx *c, const ivm_scene *scene, const ivm_params *params,

@@ -86,6 +86,8 @@ SIGNATURES = {
                                ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(_VP),
                                ctypes.POINTER(ivm_stats)], ctypes.c_int),
     "ivm_set_walk_budget": ([_VP, ctypes.c_int32], ctypes.c_int),
+    "ivm_build_edge_table": ([_VP, ctypes.POINTER(ivm_scene), ctypes.POINTER(ivm_params), _VP,
+                              ctypes.c_int32, _VP, _VP, ctypes.c_int64, _VP, _VP], ctypes.c_int),
     "ivm_validate_paths": ([_VP, ctypes.POINTER(ivm_scene), ctypes.POINTER(ivm_params), _VP, _VP,
                             ctypes.c_int64, _VP, ctypes.c_int64, ctypes.c_int32, _VP],
                            ctypes.c_int),
@@ -364,6 +366,30 @@ def ivm_build_matrix_rows(ctx, facets, s, rows, mode=IVM_MODE_EXACT, flags=0, ti
     _check(lib().ivm_build_matrix_rows(ctx.handle, scenes, len(flist), ctypes.byref(p), begin,
                                        end, ptrs, ctypes.byref(st)), "ivm_build_matrix_rows")
     return (out[0] if single else out), st
+
+
+def ivm_build_edge_table(ctx, facets, s, edges, tx, rx, mode=IVM_MODE_FILTERED, tile=0):
+    """Edge rows (uint32 [S][2][WE]) and nearest visible edge per side (int32 [S][2]),
+    both numpy; inputs numpy or torch (host or device)."""
+    def addr(x, dtype):
+        if hasattr(x, "data_ptr"):
+            return x, x.data_ptr()
+        arr = np.ascontiguousarray(x, dtype=dtype)
+        return arr, arr.ctypes.data
+
+    scenes, keep = _scenes([facets])
+    e_k, e_p = addr(edges, np.int32)
+    tx_k, tx_p = addr(tx, np.int32)
+    rx_k, rx_p = addr(rx, np.int32)
+    ne = int(e_k.shape[0]) if e_k.ndim > 1 else 0
+    S = int(tx_k.shape[0])
+    table = np.zeros((S, 2, words(ne)), dtype=np.uint32)
+    nearest = np.zeros((S, 2), dtype=np.int32)
+    p = _params(s, 0, mode, table_tile=tile)
+    _check(lib().ivm_build_edge_table(ctx.handle, scenes, ctypes.byref(p), e_p, ne, tx_p, rx_p, S,
+                                      table.ctypes.data, nearest.ctypes.data),
+           "ivm_build_edge_table")
+    return table, nearest
 
 
 def ivm_validate_paths(ctx, facets, s, tx, rx, paths, max_order, out=None):

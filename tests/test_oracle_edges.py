@@ -16,8 +16,8 @@ def bits(tab, ne):
 def test_single_box_hand_case():
     """X in front of the x = 0 wall at mid height: of the box's 8 convex edges
     only the two vertical edges of that wall and its roof edge are reachable;
-    the nearest samples (squared distance 1.25e6 cm^2) are the mid samples of
-    the two vertical edges, a tie that goes to edge 0."""
+    the nearest samples of visible edges (squared distance 1.25e6 cm^2) are
+    the mid samples of the two vertical edges, a tie that goes to edge 0."""
     F = np.asarray(sg.box_facets(*BOX, 0), np.int32)
     E = np.asarray(sg.box_edges(*BOX), np.int32)
     X = np.array([[-1000, 500, 1000]], np.int32)
@@ -45,14 +45,14 @@ def test_edge_visible_iff_some_sample_is_reachable():
             best, bd = -1, None
             for e, row in enumerate(E):
                 A, B = row[:3].astype(np.int64), row[3:].astype(np.int64)
-                free = []
+                reach, dist = [], []
                 for a in range(s):
                     p = 2 * s * A + (2 * a + 1) * (B - A)      # cell centres along the edge
-                    if not oracle.blocked(sc.facets, s, Xs, p):
-                        free.append(int(((p - Xs) ** 2).sum()))
-                assert b[t, side, e] == (len(free) > 0)
-                if free and (bd is None or min(free) < bd):
-                    best, bd = e, min(free)
+                    reach.append(not oracle.blocked(sc.facets, s, Xs, p))
+                    dist.append(int(((p - Xs) ** 2).sum()))
+                assert b[t, side, e] == any(reach)
+                if any(reach) and (bd is None or min(dist) < bd):
+                    best, bd = e, min(dist)
             assert near[t, side] == best
 
 

@@ -377,3 +377,53 @@ def edge_table(facets, s, edges, tx, rx, snaps=None, threads=None):
     with ThreadPoolExecutor(_threads(threads)) as ex:
         list(ex.map(one, range(len(snaps))))
     return tab, near
+
+
+# ---------------------------------------------- interface relations (Table I)
+
+def interface_relations(facets, M, n_facets=None):
+    """Interface relation and angular bouncing ranges of every visible ordered
+    pair (i = reference face, j = aim face, M_ij = 1), row-major
+    [Sec. II-B, Table I, Eq. (1)-(2)].
+
+    relation: 1 = PAR (normals parallel), 2 = PER (normals perpendicular),
+    0 = neither.  For edge k of face i (k = 0..3 along O -> O+U -> O+U+V ->
+    O+V), B_k is the edge's midpoint and the reference vector points from B_k
+    to the opposite edge's midpoint (the paper's BA, along the face); each
+    corner F of face j gives omega = arccos(ref . (F - B_k) / |ref| |F - B_k|)
+    in degrees (Eq. (1)), with omega >= 180 recorded as 0 (Eq. (2)); the
+    edge's range is (min, max) over j's four corners.  float64.
+    Returns (pairs int32 [P][2], relation uint8 [P], ranges float64 [P][4][2])."""
+    F = _facets(facets)
+    n = F.shape[0] if n_facets is None else n_facets
+    bits = np.unpackbits(np.ascontiguousarray(M, dtype=np.uint32).view(np.uint8),
+                         bitorder="little").reshape(n, -1)[:, :n]
+    ii, jj = np.nonzero(bits)
+    O = F[:, 0:3].astype(np.float64)
+    U = F[:, 3:6].astype(np.float64)
+    V = F[:, 6:9].astype(np.float64)
+    Ni = np.cross(F[:, 3:6].astype(np.int64), F[:, 6:9].astype(np.int64))
+    pairs = np.stack([ii, jj], axis=1).astype(np.int32)
+    rel = np.zeros(len(ii), np.uint8)
+    rng = np.zeros((len(ii), 4, 2), np.float64)
+    for p, (i, j) in enumerate(zip(ii, jj)):
+        ni, nj = Ni[i], Ni[j]
+        if not np.cross(ni, nj).any():
+            rel[p] = 1
+        elif int(ni @ nj) == 0:
+            rel[p] = 2
+        corners_j = [O[j], O[j] + U[j], O[j] + U[j] + V[j], O[j] + V[j]]
+        # edge k of face i: (start, direction), opposite edge midpoint
+        c = [O[i], O[i] + U[i], O[i] + U[i] + V[i], O[i] + V[i]]
+        for k in range(4):
+            mid = (c[k] + c[(k + 1) % 4]) / 2
+            opp = (c[(k + 2) % 4] + c[(k + 3) % 4]) / 2
+            ref = opp - mid
+            om = []
+            for Fc in corners_j:
+                d = Fc - mid
+                cosv = float(ref @ d) / (np.linalg.norm(ref) * np.linalg.norm(d))
+                w = np.degrees(np.arccos(np.clip(cosv, -1.0, 1.0)))
+                om.append(0.0 if w >= 180.0 else w)
+            rng[p, k] = (min(om), max(om))
+    return pairs, rel, rng

@@ -431,6 +431,23 @@ def run_ours(args, ws, rank, local):
         "visible_edges_mean": [float(ebits[:, 0].sum(axis=1).mean()),
                                float(ebits[:, 1].sum(axis=1).mean())],
     }
+    # interface relations and angular bouncing ranges of the step's visible
+    # pairs (Sec. II-B, Eq. (1)-(2)), timed on its own
+    rel_ms = []
+    for it in range(args.warmup + args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rpairs, rrel, _ = ivm.ivm_interface_relations(ctx, facets_d, s, M_d)
+        if it >= args.warmup:
+            rel_ms.append(1e3 * (time.perf_counter() - t0))
+    relations_out = {
+        "what": "PAR/PER relation and the four edges' angular bouncing ranges of every "
+                "visible ordered pair of the step's matrix, C-ABI call ivm_interface_relations, "
+                "results copied to host",
+        "pairs": int(len(rpairs)), "par": int((rrel == 1).sum()), "per": int((rrel == 2).sum()),
+        "ms_per_call": statistics.median(rel_ms),
+        "pairs_per_s": len(rpairs) / (statistics.median(rel_ms) / 1e3),
+    }
     rays_out = {
         "what": "image-method validation of image-tree candidates (orders 0-2) as specular "
                 f"rays, C-ABI call ivm_validate_paths, snapshots {a0}..{a1 - 1}",
@@ -476,6 +493,7 @@ def run_ours(args, ws, rank, local):
         "visibility_ranges": ranges_out,
         "ray_validation": rays_out,
         "edges": edges_out,
+        "interface_relations": relations_out,
         "forms_bit_identical": forms_agree,
         "gpu_launches": launches,
         "clocks": clk,

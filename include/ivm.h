@@ -231,6 +231,24 @@ int ivm_visibility_ranges(ivm_ctx *ctx, const ivm_scene *scene, const ivm_params
                           const uint32_t *table, ivm_range *ranges, int64_t capacity,
                           int64_t *n_ranges, ivm_range_summary *summary);
 
+/* ---------------------------------------------------- interface relations
+ * Sec. II-B, Table I, Eq. (1)-(2), for every visible ordered pair M_ij = 1
+ * (reference face i, aim face j), row-major: relation 1 = PAR (parallel
+ * normals), 2 = PER (perpendicular normals), 0 = neither; and per edge k of
+ * face i (O -> O+U -> O+U+V -> O+V), the range (min, max) over face j's
+ * corners F of the angle, in degrees, between the reference vector from the
+ * edge's midpoint B to the opposite edge's midpoint and F - B (Eq. (1)), an
+ * angle of 180 recorded as 0 (Eq. (2)).
+ *
+ * matrix [N][W] as written by ivm_build_matrix (host or device); pairs
+ * [capacity][2] int32, relation [capacity], ranges [capacity][4][2] double
+ * (host or device; pairs NULL: count only, *n_pairs gets the count).
+ * Errors: IVM_ERR_ARG, IVM_ERR_CAPACITY (capacity < *n_pairs; nothing
+ * written but the count), IVM_ERR_CUDA. */
+int ivm_interface_relations(ivm_ctx *ctx, const ivm_scene *scene, const ivm_params *params,
+                            const uint32_t *matrix, int32_t *pairs, uint8_t *relation,
+                            double *ranges, int64_t capacity, int64_t *n_pairs);
+
 /* ---------------------------------------------------------------- edges
  * Edges as visible nodes (the matrix and table list visible faces and edges:
  * Sec. I-II) and the edge nearest a source (first-order diffraction by the

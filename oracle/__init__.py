@@ -13,6 +13,7 @@ header comment of ``ivm_oracle.c``.
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 import subprocess
 from concurrent.futures import ThreadPoolExecutor
@@ -391,8 +392,11 @@ def interface_relations(facets, M, n_facets=None):
     O+V), B_k is the edge's midpoint and the reference vector points from B_k
     to the opposite edge's midpoint (the paper's BA, along the face); each
     corner F of face j gives omega = arccos(ref . (F - B_k) / |ref| |F - B_k|)
-    in degrees (Eq. (1)), with omega >= 180 recorded as 0 (Eq. (2)); the
-    edge's range is (min, max) over j's four corners.  float64.
+    in degrees (Eq. (1)), with omega = 180 recorded as 0 (Eq. (2)); the
+    edge's range is (min, max) over j's four corners.  float64; 180 degrees
+    (F - B_k opposite to the reference vector) is decided exactly on the
+    doubled integer vectors, so the Eq. (2) rule never hangs on rounding (an
+    angle just below 180 that rounds to 180.0 stays as computed).
     Returns (pairs int32 [P][2], relation uint8 [P], ranges float64 [P][4][2])."""
     F = _facets(facets)
     n = F.shape[0] if n_facets is None else n_facets
@@ -416,14 +420,18 @@ def interface_relations(facets, M, n_facets=None):
         # edge k of face i: (start, direction), opposite edge midpoint
         c = [O[i], O[i] + U[i], O[i] + U[i] + V[i], O[i] + V[i]]
         for k in range(4):
-            mid = (c[k] + c[(k + 1) % 4]) / 2
-            opp = (c[(k + 2) % 4] + c[(k + 3) % 4]) / 2
-            ref = opp - mid
+            # doubled, so that midpoints are integers
+            mid2 = (c[k] + c[(k + 1) % 4]).astype(np.int64)
+            ref2 = (c[(k + 2) % 4] + c[(k + 3) % 4]).astype(np.int64) - mid2
             om = []
             for Fc in corners_j:
-                d = Fc - mid
-                cosv = float(ref @ d) / (np.linalg.norm(ref) * np.linalg.norm(d))
-                w = np.degrees(np.arccos(np.clip(cosv, -1.0, 1.0)))
-                om.append(0.0 if w >= 180.0 else w)
+                d2 = 2 * Fc.astype(np.int64) - mid2
+                dot = int(ref2 @ d2)
+                if not np.cross(ref2, d2).any() and dot < 0:
+                    om.append(0.0)          # exactly 180 degrees: recorded as 0
+                    continue
+                cosv = dot / (math.sqrt(int(ref2 @ ref2)) * math.sqrt(int(d2 @ d2)))
+                w = math.degrees(math.acos(min(1.0, max(-1.0, cosv))))
+                om.append(w)
             rng[p, k] = (min(om), max(om))
     return pairs, rel, rng

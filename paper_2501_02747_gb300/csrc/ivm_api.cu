@@ -18,6 +18,7 @@
 #include "ivm_internal.cuh"
 #include "ranker.cuh"
 #include "edges.cuh"
+#include "relations.cuh"
 #include "ranges.cuh"
 #include "rays.cuh"
 #include "tree.cuh"
@@ -36,6 +37,7 @@ enum Slot {
     S_T_MAT, S_T_TAB, S_T_LOS, S_T_SUM, S_T_DEG, S_T_ROW, S_T_COL, S_T_WT, S_T_XA, S_T_XB,
     S_T_CNT, S_T_OFF, S_T_BS, S_T_BO, S_T_PATHS, S_T_FLAG, S_T_EXCL, S_T_RUN, S_T_START,
     S_TUNE_M, S_TUNE_T, S_TUNE_L,
+    S_REL_M, S_REL_DEG, S_REL_OFF, S_REL_BS, S_REL_BO, S_REL_PAIRS, S_REL_REL, S_REL_RNG,
     S_EDGES, S_EDGE_TAB, S_EDGE_KEY, S_EDGE_NEAR,
     S_RAY_PATHS, S_RAY_VALID,
     S_RNG_CNT, S_RNG_OFF, S_RNG_BS, S_RNG_BO, S_RNG_SUM, S_RNG_REC, S_RNG_TAB,
@@ -758,6 +760,72 @@ extern "C" int ivm_build_table(ivm_ctx *c, const ivm_scene *scenes, int32_t n_sc
     unsigned long long pairs = 0;
     for (int k = 0; k < n_scenes; k++) pairs += 2ull * hd[k].n * (unsigned long long)n_snap[k];
     return fill_stats(c, stats, pairs, 2);
+}
+
+extern "C" int ivm_interface_relations(ivm_ctx *c, const ivm_scene *scene,
+                                       const ivm_params *params, const uint32_t *matrix,
+                                       int32_t *pairs, uint8_t *relation, double *ranges,
+                                       int64_t capacity, int64_t *n_pairs)
+{
+    if (!c || !scene || !matrix || !n_pairs || capacity < 0) return IVM_ERR_ARG;
+    if (pairs && (!relation || !ranges)) return IVM_ERR_ARG;
+    int r = check_params(params);
+    if (r) return r;
+    DeviceGuard dg(c->device);
+    DevScenes g;
+    std::vector<SceneDesc> hd;
+    if ((r = plan_geometry(c, scene, 1, params->samples_per_side, g, hd))) return r;
+    const int n = hd[0].n, W = hd[0].W;
+    const bool m_host = !is_device(matrix);
+    const long long nb = (n + 255) / 256;
+    if ((r = ensure(c, S_REL_M, m_host ? sizeof(uint32_t) * (size_t)n * W : 0))) return r;
+    if ((r = ensure(c, S_REL_DEG, sizeof(long long) * (size_t)(n + 1)))) return r;
+    if ((r = ensure(c, S_REL_OFF, sizeof(long long) * (size_t)(n + 1)))) return r;
+    if ((r = ensure(c, S_REL_BS, sizeof(long long) * (size_t)(nb + 1)))) return r;
+    if ((r = ensure(c, S_REL_BO, sizeof(long long) * (size_t)(nb + 1)))) return r;
+    bind_geometry(c, g);
+    const uint32_t *M = m_host ? ptr<uint32_t>(c, S_REL_M) : matrix;
+    if (m_host)
+        CK(cudaMemcpyAsync(ptr<uint32_t>(c, S_REL_M), matrix, sizeof(uint32_t) * (size_t)n * W,
+                           cudaMemcpyHostToDevice, c->stream));
+    long long *off = ptr<long long>(c, S_REL_OFF);
+    CK(relations_count(M, n, W, ptr<long long>(c, S_REL_DEG), c->stream));
+    CK(tree_scan(ptr<long long>(c, S_REL_DEG), n, ptr<long long>(c, S_REL_BS),
+                 ptr<long long>(c, S_REL_BO), off, c->stream));
+    CK(cudaMemcpyAsync(&c->h_misc[0], off + n, sizeof(long long), cudaMemcpyDeviceToHost,
+                       c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    const long long P = (long long)c->h_misc[0];
+    *n_pairs = P;
+    if (!pairs || P == 0) return IVM_OK;
+    if (P > capacity) return IVM_ERR_CAPACITY;
+    const bool p_host = !is_device(pairs), r_host = !is_device(relation),
+               g_host = !is_device(ranges);
+    if ((r = ensure(c, S_REL_PAIRS, p_host ? sizeof(int) * 2 * (size_t)P : 0))) return r;
+    if ((r = ensure(c, S_REL_REL, r_host ? (size_t)P : 0))) return r;
+    if ((r = ensure(c, S_REL_RNG, g_host ? sizeof(double) * 8 * (size_t)P : 0))) return r;
+    bind_geometry(c, g);
+    RelArgs a;
+    a.M = m_host ? ptr<uint32_t>(c, S_REL_M) : matrix;
+    a.n = n;
+    a.W = W;
+    a.off = ptr<long long>(c, S_REL_OFF);
+    a.pairs = p_host ? ptr<int>(c, S_REL_PAIRS) : pairs;
+    a.relation = r_host ? ptr<uint8_t>(c, S_REL_REL) : relation;
+    a.ranges = g_host ? ptr<double>(c, S_REL_RNG) : ranges;
+    if ((r = enqueue_geometry(c, g, scene, hd, hd.data(), true))) return r;   // the leaves
+    CK(relations_write(g, a, c->stream));
+    if ((r = read_error(c))) return r;
+    if (p_host)
+        CK(cudaMemcpyAsync(pairs, a.pairs, sizeof(int) * 2 * (size_t)P, cudaMemcpyDeviceToHost,
+                           c->stream));
+    if (r_host)
+        CK(cudaMemcpyAsync(relation, a.relation, (size_t)P, cudaMemcpyDeviceToHost, c->stream));
+    if (g_host)
+        CK(cudaMemcpyAsync(ranges, a.ranges, sizeof(double) * 8 * (size_t)P,
+                           cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return IVM_OK;
 }
 
 extern "C" int ivm_build_edge_table(ivm_ctx *c, const ivm_scene *scene, const ivm_params *params,

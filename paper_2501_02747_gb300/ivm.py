@@ -86,6 +86,9 @@ SIGNATURES = {
                                ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(_VP),
                                ctypes.POINTER(ivm_stats)], ctypes.c_int),
     "ivm_set_walk_budget": ([_VP, ctypes.c_int32], ctypes.c_int),
+    "ivm_interface_relations": ([_VP, ctypes.POINTER(ivm_scene), ctypes.POINTER(ivm_params), _VP,
+                                 _VP, _VP, _VP, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)],
+                                ctypes.c_int),
     "ivm_build_edge_table": ([_VP, ctypes.POINTER(ivm_scene), ctypes.POINTER(ivm_params), _VP,
                               ctypes.c_int32, _VP, _VP, ctypes.c_int64, _VP, _VP], ctypes.c_int),
     "ivm_validate_paths": ([_VP, ctypes.POINTER(ivm_scene), ctypes.POINTER(ivm_params), _VP, _VP,
@@ -366,6 +369,30 @@ def ivm_build_matrix_rows(ctx, facets, s, rows, mode=IVM_MODE_EXACT, flags=0, ti
     _check(lib().ivm_build_matrix_rows(ctx.handle, scenes, len(flist), ctypes.byref(p), begin,
                                        end, ptrs, ctypes.byref(st)), "ivm_build_matrix_rows")
     return (out[0] if single else out), st
+
+
+def ivm_interface_relations(ctx, facets, s, matrix):
+    """(pairs int32 [P][2], relation uint8 [P], ranges float64 [P][4][2]) of the
+    visible ordered pairs of `matrix` (numpy or torch, host or device)."""
+    scenes, keep = _scenes([facets])
+    if hasattr(matrix, "data_ptr"):
+        m_k, m_p = matrix, matrix.data_ptr()
+    else:
+        m_k = np.ascontiguousarray(matrix).view(np.uint32)
+        m_p = m_k.ctypes.data
+    p = _params(s)
+    n = ctypes.c_int64(0)
+    _check(lib().ivm_interface_relations(ctx.handle, scenes, ctypes.byref(p), m_p, None, None,
+                                         None, 0, ctypes.byref(n)), "ivm_interface_relations")
+    P = n.value
+    pairs = np.zeros((P, 2), np.int32)
+    rel = np.zeros(P, np.uint8)
+    rng = np.zeros((P, 4, 2), np.float64)
+    if P:
+        _check(lib().ivm_interface_relations(ctx.handle, scenes, ctypes.byref(p), m_p,
+                                             pairs.ctypes.data, rel.ctypes.data, rng.ctypes.data,
+                                             P, ctypes.byref(n)), "ivm_interface_relations")
+    return pairs, rel, rng
 
 
 def ivm_build_edge_table(ctx, facets, s, edges, tx, rx, mode=IVM_MODE_FILTERED, tile=0):

@@ -89,6 +89,11 @@ def lib():
                                         ctypes.c_int32, _i32p, _i32p, ctypes.c_int64,
                                         ctypes.c_int64, _u32p, _i32p]
         L.oracle_edge_table.restype = None
+        L.oracle_edge_matrix_rows.argtypes = [_i32p, ctypes.c_int32, ctypes.c_int32, _i32p,
+                                              _i32p, ctypes.c_int32, ctypes.c_int32,
+                                              ctypes.c_int32, _u32p, ctypes.c_int32,
+                                              ctypes.c_int32, _u32p]
+        L.oracle_edge_matrix_rows.restype = None
         _lib = L
     return _lib
 
@@ -378,6 +383,41 @@ def edge_table(facets, s, edges, tx, rx, snaps=None, threads=None):
     with ThreadPoolExecutor(_threads(threads)) as ex:
         list(ex.map(one, range(len(snaps))))
     return tab, near
+
+
+def edge_matrix(facets, s, edges, edge_faces, fe_rows=None, ee_rows=None, threads=None):
+    """Edges as rows and columns of the matrix (step 10 of ivm_oracle.c):
+    (fe uint32 [len(fe_rows)][WE] = the facet rows' edge bits,
+     ee uint32 [len(ee_rows)][WE] = the edge rows' edge bits).  Rows default
+    to all; the edge -> facet block is the transpose of fe."""
+    F = _facets(facets)
+    E = np.ascontiguousarray(edges, dtype=np.int32).reshape(-1, 6)
+    EF = np.ascontiguousarray(edge_faces, dtype=np.int32).reshape(-1, 2)
+    assert EF.shape[0] == E.shape[0]
+    n, ne = F.shape[0], E.shape[0]
+    fe_rows = np.arange(n) if fe_rows is None else np.asarray(fe_rows, dtype=np.int64)
+    ee_rows = np.arange(ne) if ee_rows is None else np.asarray(ee_rows, dtype=np.int64)
+    WE = words(ne)
+    fe = np.zeros((len(fe_rows), WE), dtype=np.uint32)
+    ee = np.zeros((len(ee_rows), WE), dtype=np.uint32)
+    empty = np.zeros(1, dtype=np.uint32)
+    L = lib()
+
+    def one(job):
+        kind, k = job
+        if kind == 0:
+            i = int(fe_rows[k])
+            L.oracle_edge_matrix_rows(_p(F, _i32p), n, s, _p(E, _i32p), _p(EF, _i32p), ne, i,
+                                      i + 1, _p(fe[k], _u32p), 0, 0, _p(empty, _u32p))
+        else:
+            e = int(ee_rows[k])
+            L.oracle_edge_matrix_rows(_p(F, _i32p), n, s, _p(E, _i32p), _p(EF, _i32p), ne, 0, 0,
+                                      _p(empty, _u32p), e, e + 1, _p(ee[k], _u32p))
+
+    jobs = [(0, k) for k in range(len(fe_rows))] + [(1, k) for k in range(len(ee_rows))]
+    with ThreadPoolExecutor(_threads(threads)) as ex:
+        list(ex.map(one, jobs))
+    return fe, ee
 
 
 # ---------------------------------------------- interface relations (Table I)

@@ -400,6 +400,66 @@ OR_EXPORT void oracle_edge_table(const int32_t *facets, int32_t n, int32_t s,
     free(F);
 }
 
+/* step 10: edges as rows and columns of the matrix.  Edge e (A -> B, cm)
+ * has s samples q_b = 2s A + (2b+1)(B - A) and two adjacent facets f1, f2
+ * (edge_faces[2e], edge_faces[2e+1]); a point P reaches the edge from outside
+ * its building only when it is strictly in front of f1 or f2 (ext).
+ *   fe[i][e] = exists facet sample p, edge sample q: front(q, i), ext(p, e),
+ *              not blocked(p, q);
+ *   ee[e][g] = e != g and exists q on e, r on g: ext(r, e), ext(q, g),
+ *              not blocked(q, r).
+ * Rows [fe0, fe1) of fe and [ee0, ee1) of ee, WE = ceil(ne / 32) words each. */
+static V edge_sample(const int32_t *E, int s, int b)
+{
+    V A = scl(2 * (i128)s, mk(E[0], E[1], E[2]));
+    return add(A, scl(2 * b + 1, sub(mk(E[3], E[4], E[5]), mk(E[0], E[1], E[2]))));
+}
+
+static int ext(V P, const Facet *F, const int32_t *ef, int32_t e)
+{
+    return front(P, &F[ef[2 * e]]) || front(P, &F[ef[2 * e + 1]]);
+}
+
+OR_EXPORT void oracle_edge_matrix_rows(const int32_t *facets, int32_t n, int32_t s,
+                                       const int32_t *edges, const int32_t *edge_faces,
+                                       int32_t ne, int32_t fe0, int32_t fe1, uint32_t *fe,
+                                       int32_t ee0, int32_t ee1, uint32_t *ee)
+{
+    int32_t WE = oracle_words(ne);
+    Facet *F = load_facets(facets, n, s);
+    memset(fe, 0, sizeof(uint32_t) * (size_t)WE * (size_t)(fe1 - fe0));
+    memset(ee, 0, sizeof(uint32_t) * (size_t)WE * (size_t)(ee1 - ee0));
+    for (int32_t i = fe0; i < fe1; i++)
+        for (int32_t e = 0; e < ne; e++) {
+            int vis = 0;
+            for (int b = 0; b < s && !vis; b++) {
+                V q = edge_sample(edges + 6 * (size_t)e, s, b);
+                if (!front(q, &F[i])) continue;
+                for (int a0 = 0; a0 < s && !vis; a0++)
+                    for (int a1 = 0; a1 < s && !vis; a1++) {
+                        V p = sample(&F[i], s, a0, a1);
+                        if (ext(p, F, edge_faces, e) && !blocked(F, n, p, q)) vis = 1;
+                    }
+            }
+            if (vis) fe[(size_t)(i - fe0) * WE + (e >> 5)] |= 1u << (e & 31);
+        }
+    for (int32_t e = ee0; e < ee1; e++)
+        for (int32_t g = 0; g < ne; g++) {
+            if (g == e) continue;
+            int vis = 0;
+            for (int b = 0; b < s && !vis; b++) {
+                V q = edge_sample(edges + 6 * (size_t)e, s, b);
+                if (!ext(q, F, edge_faces, g)) continue;
+                for (int c = 0; c < s && !vis; c++) {
+                    V r = edge_sample(edges + 6 * (size_t)g, s, c);
+                    if (ext(r, F, edge_faces, e) && !blocked(F, n, q, r)) vis = 1;
+                }
+            }
+            if (vis) ee[(size_t)(e - ee0) * WE + (g >> 5)] |= 1u << (g & 31);
+        }
+    free(F);
+}
+
 /* Number of sample pairs (p_a on i, q_b on j) that satisfy the three
  * conditions of step 4 (for the hand-counted partial-blocker scene). */
 OR_EXPORT int64_t oracle_pair_free_count(const int32_t *facets, int32_t n, int32_t s, int32_t i,

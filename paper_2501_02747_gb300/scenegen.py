@@ -99,6 +99,24 @@ def box_edges(x0, y0, x1, y1, h):
     ]
 
 
+def box_edge_faces(base):
+    """The two facets meeting at each edge of box_edges, for a box whose
+    box_facets rows start at index `base` (roof, walls y0, y1, x1, x0)."""
+    roof, wy0, wy1, wx1, wx0 = range(base, base + 5)
+    return [(wy0, wx0), (wy0, wx1), (wy1, wx1), (wy1, wx0),
+            (roof, wy0), (roof, wx1), (roof, wy1), (roof, wx0)]
+
+
+def edge_faces_of(scene, with_ground=True) -> np.ndarray:
+    """Adjacent facets of edges_of(scene), int32 [E][2], for facets laid out by
+    facets_from_boxes (the ground first, then five rows per box)."""
+    first = 1 if with_ground else 0
+    rows = []
+    for b in range(len(scene.boxes)):
+        rows.extend(box_edge_faces(first + 5 * b))
+    return np.asarray(rows, dtype=np.int32).reshape(-1, 2)
+
+
 def edges_of(scene) -> np.ndarray:
     """Convex edges of a scene's box buildings, int32 [E][6] (endpoints, cm)."""
     rows = []

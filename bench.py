@@ -46,7 +46,7 @@ FP32_OPS_PER_FILTERED_LEAF = 104  # 4 edges x 26 (value, permanent, bound, compa
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -103,10 +103,18 @@ class Clocks:
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.fh,
+                 "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.fh,
                 stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+            return
+        # the sampler takes a moment to start: wait for its first sample so that
+        # the samples cover the timed region that follows
+        t0 = time.time()
+        while time.time() - t0 < 5.0 and self.proc.poll() is None:
+            if os.path.getsize(self.path) > 0:
+                break
+            time.sleep(0.05)
 
     def stop(self):
         if self.proc is None:
@@ -431,6 +439,29 @@ def run_ours(args, ws, rank, local):
         "visible_edges_mean": [float(ebits[:, 0].sum(axis=1).mean()),
                                float(ebits[:, 1].sum(axis=1).mean())],
     }
+    # edges as matrix rows and columns: facet-edge and edge-edge visibility
+    # (Sec. I-II, Sec. III-B), timed on its own, outputs left on the device
+    EF_d = torch.from_numpy(sg.edge_faces_of(sc)).to(dev)
+    ne = int(E_d.shape[0])
+    fe_d = torch.zeros((N, (ne + 31) // 32), dtype=torch.int32, device=dev)
+    ee_d = torch.zeros((ne, (ne + 31) // 32), dtype=torch.int32, device=dev)
+    em_ms = []
+    for it in range(args.warmup + args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ivm.ivm_build_edge_matrix(ctx, facets_d, s, E_d, EF_d, out=(fe_d, ee_d))
+        if it >= args.warmup:
+            em_ms.append(1e3 * (time.perf_counter() - t0))
+    fe_bits = int(np.unpackbits(fe_d.cpu().numpy().view(np.uint8)).sum())
+    ee_bits = int(np.unpackbits(ee_d.cpu().numpy().view(np.uint8)).sum())
+    edge_matrix_out = {
+        "what": "edges as matrix rows and columns: facet-edge bits fe [N][WE] and edge-edge "
+                "bits ee [E][WE], C-ABI call ivm_build_edge_matrix, outputs on the device",
+        "facet_edge_pairs": N * ne, "edge_edge_pairs": ne * (ne - 1) // 2,
+        "ms_per_call": statistics.median(em_ms),
+        "pair_tests_per_s": (N * ne + ne * (ne - 1) // 2) / (statistics.median(em_ms) / 1e3),
+        "facet_edge_bits": fe_bits, "edge_edge_bits": ee_bits,
+    }
     # interface relations and angular bouncing ranges of the step's visible
     # pairs (Sec. II-B, Eq. (1)-(2)), timed on its own
     rel_ms = []
@@ -493,6 +524,7 @@ def run_ours(args, ws, rank, local):
         "visibility_ranges": ranges_out,
         "ray_validation": rays_out,
         "edges": edges_out,
+        "edge_matrix": edge_matrix_out,
         "interface_relations": relations_out,
         "forms_bit_identical": forms_agree,
         "gpu_launches": launches,

@@ -269,6 +269,27 @@ int ivm_build_edge_table(ivm_ctx *ctx, const ivm_scene *scene, const ivm_params 
                          const int32_t *edges, int32_t n_edges, const int32_t *tx,
                          const int32_t *rx, int64_t n_snap, uint32_t *table, int32_t *nearest);
 
+/* Edges as rows and columns of the matrix (Sec. I-II: per face or edge, the
+ * visible faces and edges; the nodes of first-order diffraction, Sec. III-B).
+ * Edge e is edges[6e..6e+5] as above, with s samples, and edge_faces[2e],
+ * edge_faces[2e+1] are the two facets (scene indices) that meet at it; a
+ * point P reaches the edge from outside only when P is strictly in front of
+ * one of them (ext).  fe[i][e] = 1 when some sample p of facet i and some
+ * sample q of edge e have q strictly in front of i, ext(p, e) and the open
+ * segment p-q meets no closed facet; ee[e][g] = 1 (e != g) when some samples
+ * q of e and r of g have ext(r, e), ext(q, g) and q-r unblocked (ee is
+ * symmetric).  The edge -> facet block of the full matrix is fe transposed.
+ *
+ * edges [n_edges][6], edge_faces [n_edges][2], fe [N][WE], ee [n_edges][WE]
+ * (WE = ceil(n_edges / 32), padding bits 0): host or device.  params:
+ * samples_per_side and mode (IVM_MODE_EXACT or IVM_MODE_FILTERED, the same
+ * bits).  Errors: IVM_ERR_ARG (n_edges < 0, a null buffer, an adjacent facet
+ * index outside 0..N-1), IVM_ERR_RANGE (an edge sample out of range),
+ * IVM_ERR_TIMEOUT, IVM_ERR_CUDA. */
+int ivm_build_edge_matrix(ivm_ctx *ctx, const ivm_scene *scene, const ivm_params *params,
+                          const int32_t *edges, const int32_t *edge_faces, int32_t n_edges,
+                          uint32_t *fe, uint32_t *ee);
+
 /* ------------------------------------------------- ray validation
  * The image method on image-tree candidates (Sec. IV-B: the pre-processed
  * image tree and the brute-force method give the same valid rays).  For path

@@ -38,6 +38,7 @@ enum Slot {
     S_T_CNT, S_T_OFF, S_T_BS, S_T_BO, S_T_PATHS, S_T_FLAG, S_T_EXCL, S_T_RUN, S_T_START,
     S_TUNE_M, S_TUNE_T, S_TUNE_L,
     S_REL_M, S_REL_DEG, S_REL_OFF, S_REL_BS, S_REL_BO, S_REL_PAIRS, S_REL_REL, S_REL_RNG,
+    S_EM_EDGES, S_EM_FACES, S_EM_FE, S_EM_EE, S_EM_WORK,
     S_EDGES, S_EDGE_TAB, S_EDGE_KEY, S_EDGE_NEAR,
     S_RAY_PATHS, S_RAY_VALID,
     S_RNG_CNT, S_RNG_OFF, S_RNG_BS, S_RNG_BO, S_RNG_SUM, S_RNG_REC, S_RNG_TAB,
@@ -887,6 +888,62 @@ extern "C" int ivm_build_edge_table(ivm_ctx *c, const ivm_scene *scene, const iv
                            c->stream));
     if (n_host)
         CK(cudaMemcpyAsync(nearest, a.nearest, sizeof(int) * 2 * S, cudaMemcpyDeviceToHost,
+                           c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return IVM_OK;
+}
+
+extern "C" int ivm_build_edge_matrix(ivm_ctx *c, const ivm_scene *scene,
+                                     const ivm_params *params, const int32_t *edges,
+                                     const int32_t *edge_faces, int32_t n_edges, uint32_t *fe,
+                                     uint32_t *ee)
+{
+    if (!c || !scene || n_edges < 0) return IVM_ERR_ARG;
+    if (n_edges > 0 && (!edges || !edge_faces || !fe || !ee)) return IVM_ERR_ARG;
+    int r = check_params(params);
+    if (r) return r;
+    DeviceGuard dg(c->device);
+    DevScenes g;
+    std::vector<SceneDesc> hd;
+    if ((r = plan_geometry(c, scene, 1, params->samples_per_side, g, hd))) return r;
+    if (n_edges == 0) return IVM_OK;
+    const int n = hd[0].n, WE = words(n_edges);
+    const size_t ne = (size_t)n_edges;
+    const bool e_host = !is_device(edges), f_host = !is_device(edge_faces);
+    const bool fe_host = !is_device(fe), ee_host = !is_device(ee);
+    if ((r = ensure(c, S_EM_EDGES, e_host ? sizeof(int) * 6 * ne : 0))) return r;
+    if ((r = ensure(c, S_EM_FACES, f_host ? sizeof(int) * 2 * ne : 0))) return r;
+    if ((r = ensure(c, S_EM_FE, fe_host ? sizeof(uint32_t) * (size_t)n * WE : 0))) return r;
+    if ((r = ensure(c, S_EM_EE, ee_host ? sizeof(uint32_t) * ne * WE : 0))) return r;
+    if ((r = ensure(c, S_EM_WORK, sizeof(unsigned long long)))) return r;
+    bind_geometry(c, g);
+    EdgeMatrixArgs a;
+    a.edges = e_host ? ptr<int>(c, S_EM_EDGES) : edges;
+    a.faces = f_host ? ptr<int>(c, S_EM_FACES) : edge_faces;
+    a.n = n;
+    a.ne = n_edges;
+    a.WE = WE;
+    a.fe = fe_host ? ptr<uint32_t>(c, S_EM_FE) : fe;
+    a.ee = ee_host ? ptr<uint32_t>(c, S_EM_EE) : ee;
+    a.tile = 4;
+    a.work = ptr<unsigned long long>(c, S_EM_WORK);
+    a.ctr = c->d_ctr;
+    if (e_host)
+        CK(cudaMemcpyAsync(ptr<int>(c, S_EM_EDGES), edges, sizeof(int) * 6 * ne,
+                           cudaMemcpyHostToDevice, c->stream));
+    if (f_host)
+        CK(cudaMemcpyAsync(ptr<int>(c, S_EM_FACES), edge_faces, sizeof(int) * 2 * ne,
+                           cudaMemcpyHostToDevice, c->stream));
+    if ((r = enqueue_geometry(c, g, scene, hd, hd.data(), true))) return r;
+    CK(cudaMemsetAsync(a.fe, 0, sizeof(uint32_t) * (size_t)n * WE, c->stream));
+    CK(cudaMemsetAsync(a.ee, 0, sizeof(uint32_t) * ne * WE, c->stream));
+    CK(edges_matrix(g, a, params->mode != IVM_MODE_EXACT, c->n_sm, c->d_err, c->stream));
+    if ((r = read_error(c))) return r;
+    if (fe_host)
+        CK(cudaMemcpyAsync(fe, a.fe, sizeof(uint32_t) * (size_t)n * WE, cudaMemcpyDeviceToHost,
+                           c->stream));
+    if (ee_host)
+        CK(cudaMemcpyAsync(ee, a.ee, sizeof(uint32_t) * ne * WE, cudaMemcpyDeviceToHost,
                            c->stream));
     CK(cudaStreamSynchronize(c->stream));
     return IVM_OK;

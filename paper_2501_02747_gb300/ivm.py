@@ -86,6 +86,8 @@ SIGNATURES = {
                                ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(_VP),
                                ctypes.POINTER(ivm_stats)], ctypes.c_int),
     "ivm_set_walk_budget": ([_VP, ctypes.c_int32], ctypes.c_int),
+    "ivm_build_edge_matrix": ([_VP, ctypes.POINTER(ivm_scene), ctypes.POINTER(ivm_params), _VP,
+                               _VP, ctypes.c_int32, _VP, _VP], ctypes.c_int),
     "ivm_interface_relations": ([_VP, ctypes.POINTER(ivm_scene), ctypes.POINTER(ivm_params), _VP,
                                  _VP, _VP, _VP, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)],
                                 ctypes.c_int),
@@ -369,6 +371,31 @@ def ivm_build_matrix_rows(ctx, facets, s, rows, mode=IVM_MODE_EXACT, flags=0, ti
     _check(lib().ivm_build_matrix_rows(ctx.handle, scenes, len(flist), ctypes.byref(p), begin,
                                        end, ptrs, ctypes.byref(st)), "ivm_build_matrix_rows")
     return (out[0] if single else out), st
+
+
+def ivm_build_edge_matrix(ctx, facets, s, edges, edge_faces, mode=IVM_MODE_FILTERED, out=None):
+    """(fe uint32 [N][WE], ee uint32 [E][WE]): edges as matrix rows and columns.
+    Host inputs give numpy outputs; `out` = (fe, ee) torch device tensors to
+    write in place."""
+    scenes, keep = _scenes([facets])
+    n = int(facets.shape[0])
+    E = edges if hasattr(edges, "data_ptr") else np.ascontiguousarray(edges, np.int32).reshape(-1, 6)
+    EF = edge_faces if hasattr(edge_faces, "data_ptr") else \
+        np.ascontiguousarray(edge_faces, np.int32).reshape(-1, 2)
+    ne = int(E.shape[0])
+    WE = (ne + 31) // 32
+    if out is None:
+        fe = np.zeros((n, WE), np.uint32)
+        ee = np.zeros((ne, WE), np.uint32)
+        fe_p, ee_p = fe.ctypes.data, ee.ctypes.data
+    else:
+        fe, ee = out
+        fe_p, ee_p = fe.data_ptr(), ee.data_ptr()
+    ptr = lambda x: x.data_ptr() if hasattr(x, "data_ptr") else x.ctypes.data
+    p = _params(s, mode=mode)
+    _check(lib().ivm_build_edge_matrix(ctx.handle, scenes, ctypes.byref(p), ptr(E), ptr(EF), ne,
+                                       fe_p, ee_p), "ivm_build_edge_matrix")
+    return fe, ee
 
 
 def ivm_interface_relations(ctx, facets, s, matrix):

@@ -78,6 +78,8 @@ extern "C" {
 #define IVM_FLAG_GRAPH 2       /* replay the call's launches as a CUDA graph */
 #define IVM_FLAG_OCCLUDER_CACHE 4 /* test each warp's last blockers before the BVH */
 #define IVM_FLAG_DEDUP_SOURCES 8  /* table: trace one row per run of equal positions */
+#define IVM_FLAG_NO_SPLIT 16      /* table, persistent: no lazy splitting of snapshot ranges
+                                     (idle warps otherwise take half of a busy warp's rest) */
 
 typedef struct ivm_facet {
     int32_t o[3], u[3], v[3]; /* cm; u x v points outward */

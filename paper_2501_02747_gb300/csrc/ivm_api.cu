@@ -76,6 +76,7 @@ struct ivm_ctx {
     int *d_err = nullptr;                 // device error word
     unsigned long long *d_ctr = nullptr;  // C_COUNT_ counters
     unsigned long long *d_misc = nullptr; // [0] pair count, [1] cursor, [2] work queue
+    void *d_steal = nullptr;              // table: lazy-splitting slots, 64 x 16 B per SM
     int *h_err = nullptr;
     unsigned long long *h_ctr = nullptr, *h_misc = nullptr;
     cudaEvent_t ev[8] = {};
@@ -455,6 +456,7 @@ extern "C" int ivm_create(ivm_ctx **out, int device, void *cuda_stream)
     CK(cudaMalloc(&c->d_err, sizeof(int)));
     CK(cudaMalloc(&c->d_ctr, sizeof(unsigned long long) * C_COUNT_));
     CK(cudaMalloc(&c->d_misc, sizeof(unsigned long long) * 4));
+    CK(cudaMalloc(&c->d_steal, 16 * 64 * (size_t)c->n_sm));
     CK(cudaMallocHost(&c->h_err, sizeof(int)));
     CK(cudaMallocHost(&c->h_ctr, sizeof(unsigned long long) * C_COUNT_));
     CK(cudaMallocHost(&c->h_misc, sizeof(unsigned long long) * 4));
@@ -478,6 +480,7 @@ extern "C" int ivm_destroy(ivm_ctx *c)
     cudaFree(c->d_err);
     cudaFree(c->d_ctr);
     cudaFree(c->d_misc);
+    cudaFree(c->d_steal);
     cudaFreeHost(c->h_err);
     cudaFreeHost(c->h_ctr);
     cudaFreeHost(c->h_misc);
@@ -673,7 +676,11 @@ extern "C" int ivm_build_table(ivm_ctx *c, const ivm_scene *scenes, int32_t n_sc
         if (tx_host[k]) pos_tx += 3 * S;
         if (rx_host[k]) pos_rx += 3 * S;
     }
-    const LaunchCfg cfg = launch_cfg(c, params);
+    LaunchCfg cfg = launch_cfg(c, params);
+    // lazy splitting keeps snapshot indices in 32 bits and work items below 2^32
+    bool splittable = !(params->flags & IVM_FLAG_NO_SPLIT) && items < (1LL << 32) - 2;
+    for (int k = 0; k < n_scenes; k++) splittable &= n_snap[k] < (1LL << 31);
+    if (cfg.persistent && splittable) cfg.steal = c->d_steal;
     const bool sync_free = cfg.persistent;
     const bool use_graph = (params->flags & IVM_FLAG_GRAPH) && all_device;
     if ((r = ensure(c, S_OUT, sizeof(uint32_t) * host_tab))) return r;

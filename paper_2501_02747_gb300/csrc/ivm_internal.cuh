@@ -132,6 +132,7 @@ struct LaunchCfg {
     int dedup;            // table: compute one row per run of equal source positions
     const unsigned long long *count_dev = nullptr;  // matrix, persistent: device pair count
     LearnedDev learn;     // matrix, learned form (ranks == nullptr: off)
+    void *steal = nullptr;// table, persistent: 16-byte slots, 64 per SM (nullptr: no splitting)
 };
 
 cudaError_t launch_matrix(const DevScenes &g, const int2 *pairs, unsigned long long npairs,

@@ -33,6 +33,18 @@
 // the tile, and j is hidden at all of the tile's snapshots.  F is the facet
 // that hid j at the tile's first traced snapshot; the two end tests per
 // sample are the same exact facet tests as everywhere else.
+//
+// Lazy splitting (persistent launches).  A work item is a long dependent
+// chain, and a few long items decide the kernel's span.  Each warp publishes
+// the snapshot range it still has to do, [cur, end), in a 16-byte slot; a
+// warp that finds the queue empty takes the back half of the largest
+// remaining range by one 128-bit compare-and-swap that lowers the owner's
+// end (only while both halves keep at least one straight stretch).  The
+// owner republishes cur by compare-and-swap at each stretch and never runs
+// past the end it reads there; the split point is at least one stretch past
+// the published cur, so no snapshot is done twice and none is left out.
+// Nobody waits: an owner never depends on a thief, and a thief that finds
+// nothing worth taking exits.
 #include "ivm_internal.cuh"
 #include "traverse.cuh"
 #include "filter.cuh"
@@ -51,6 +63,56 @@ constexpr bool kTableSampleBlockers = true;
 constexpr int kSampleSlots = 32 * 32;
 // Snapshots per straight-stretch proof (a work item may hold several).
 constexpr int kProofTile = 16;
+
+// ------------------------------------------------------------ lazy splitting
+
+// a = work item + 1 (0: never used); b = cur | end << 32 (local snapshots)
+struct __align__(16) StealSlot {
+    unsigned long long a, b;
+};
+
+__device__ __forceinline__ bool same(const StealSlot &x, const StealSlot &y)
+{
+    return x.a == y.a && x.b == y.b;
+}
+
+__device__ __forceinline__ StealSlot slot_read(StealSlot *p)
+{
+    return atomicCAS(p, StealSlot{0ull, 0ull}, StealSlot{0ull, 0ull});   // atomic 128-bit load
+}
+
+__device__ __forceinline__ unsigned long long pack_range(long long cur, long long end)
+{
+    return (unsigned long long)(unsigned)cur | ((unsigned long long)(unsigned)end << 32);
+}
+
+// Sets the owner's cur and returns its current end.  Thieves only ever lower
+// end, so the loop ends after at most one retry per successful split.
+__device__ __noinline__ long long slot_publish(StealSlot *p, long long cur)
+{
+    StealSlot old = slot_read(p);
+    for (int k = 0; k < 64; k++) {
+        const StealSlot want{old.a, pack_range(cur, (long long)(old.b >> 32))};
+        const StealSlot got = atomicCAS(p, old, want);
+        if (same(got, old)) return (long long)(old.b >> 32);
+        old = got;
+    }
+    // never reached in practice; the range read last is still a valid bound
+    // (a thief that split after it redoes at most the same snapshots)
+    return (long long)(old.b >> 32);
+}
+
+__device__ __forceinline__ void slot_start(StealSlot *p, long long item, long long cur,
+                                           long long end)
+{
+    StealSlot old = slot_read(p);
+    const StealSlot want{(unsigned long long)item + 1ull, pack_range(cur, end)};
+    for (int k = 0; k < 64; k++) {
+        const StealSlot got = atomicCAS(p, old, want);
+        if (same(got, old)) return;
+        old = got;
+    }
+}
 
 __device__ __forceinline__ int scene_of_snap(const SceneDesc *desc, int n_scenes, long long T)
 {
@@ -331,8 +393,11 @@ __device__ __noinline__ bool tile_on_segment(const int *pos, long long t0, long 
     return __all_sync(kFull, ok);
 }
 
+// Snapshots [tb, te) of work item `item` (tb < 0: the item's whole tile).
+// With a slot, the range's end is re-read from it at every stretch.
 template <bool CACHE, class LeafFn>
-__device__ __forceinline__ void table_tile(const DevScenes &g, long long item, int TT,
+__device__ __noinline__ void table_tile(const DevScenes &g, long long item, int TT,
+                                           long long tb, long long te, StealSlot *slot,
                                            const int *rep, int *err, WalkCounters &wc,
                                            LeafFn leaf, OccluderCache &cache, int *sblk)
 {
@@ -344,8 +409,14 @@ __device__ __forceinline__ void table_tile(const DevScenes &g, long long item, i
     const int side = local >= per_side ? 1 : 0;
     const long long rem = local - side * per_side;
     const int c = (int)(rem / D.ntiles);
-    const long long t0 = (rem - (long long)c * D.ntiles) * TT;
-    const long long t1 = min(t0 + TT, D.nsnap);
+    long long t0 = (rem - (long long)c * D.ntiles) * TT;
+    long long t1 = min(t0 + TT, D.nsnap);
+    if (tb >= 0) {
+        t0 = tb;
+        t1 = te;
+    } else if (slot && lane == 0) {
+        slot_start(slot, item, t0, t1);
+    }
     if (CACHE) cache.enter_scene(sc);
     const int *pos = side ? D.rx : D.tx;
     const int jl = 32 * c + lane;
@@ -366,7 +437,18 @@ __device__ __forceinline__ void table_tile(const DevScenes &g, long long item, i
         __syncwarp();
     }
     for (long long u0 = t0; u0 < t1; u0 += kProofTile) {   // straight-stretch proofs
+        if (slot) {
+            long long end = 0;
+            if (lane == 0) end = slot_publish(slot, u0);
+            t1 = min(t1, __shfl_sync(kFull, end, 0));
+            if (u0 >= t1) break;
+        }
         const long long u1 = min(u0 + (long long)kProofTile, t1);
+        if (rep) {   // a stretch whose rows are all copied later needs nothing
+            const long long t = u0 + lane;
+            const bool traced = t < u1 && rep[2 * (D.snap0 + t) + side] == t;
+            if (!__any_sync(kFull, traced)) continue;
+        }
         bool proof = CACHE && kTableTileProof && u1 - u0 >= 3 &&
                      tile_on_segment(pos, u0, u1, k);
         unsigned hidden = 0;   // facets settled hidden for snapshots [u0, u1)
@@ -510,6 +592,7 @@ __device__ __forceinline__ void table_tile(const DevScenes &g, long long item, i
             }
         }
     }
+    if (slot && lane == 0) slot_publish(slot, t1);   // done: nothing left to take
 }
 
 template <bool CACHE, class LeafFn>
@@ -553,11 +636,83 @@ __device__ __forceinline__ void los_item(const DevScenes &g, long long chunk, in
 // and 4 keeps the per-snapshot state in registers (8 spills 1.5 KB a thread).
 constexpr int kTableMinBlocks = 4;
 
+// A warp whose queue is empty: take the back half of the largest remaining
+// range (at least two stretches) in a window of slots, do it, and look again;
+// exit when a full scan finds no range worth splitting.  Windows start at a
+// pseudo-random slot per warp and round, so that idle warps spread over the
+// busy ones instead of all racing for the same range.  The scan's plain
+// loads may be stale or torn: they only propose the compare value of the
+// swap, which then fails.
+constexpr int kStealWindow = 256;
+constexpr int kStealMin = 2 * kProofTile;   // smallest remaining range worth splitting
+
+template <bool CACHE, class LeafFn>
+__device__ __forceinline__ void steal_loop(const DevScenes &g, int TT, StealSlot *slots,
+                                           StealSlot *mine, const int *rep, int *err,
+                                           WalkCounters &wc, LeafFn leaf, OccluderCache &cache,
+                                           int *sblk)
+{
+    const int lane = threadIdx.x & 31;
+    const int nslots = (int)(gridDim.x * (blockDim.x >> 5));
+    const unsigned me = (unsigned)(mine - slots);
+    bool full = nslots <= kStealWindow;   // the next scan covers every slot
+    for (int round = 0; round < (1 << 20); round++) {
+        long long best_rem = 0;
+        int best = -1;
+        unsigned long long sa = 0, sb = 0;
+        unsigned h = (me + 1u) * 0x9E3779B1u ^ (unsigned)round * 0x85EBCA77u;
+        h ^= h >> 15;
+        h *= 0x2C1B3C6Du;
+        h ^= h >> 12;
+        const int start = full ? 0 : (int)(h % (unsigned)nslots);
+        const int span = full ? nslots : kStealWindow;
+        for (int k = lane; k < span; k += 32) {
+            int i = start + k;
+            if (i >= nslots) i -= nslots;
+            const unsigned long long a = __ldcg(&slots[i].a), b = __ldcg(&slots[i].b);
+            const long long rem = (long long)(b >> 32) - (long long)(unsigned)b;
+            if (a != 0ull && rem > best_rem) {
+                best_rem = rem;
+                best = i;
+                sa = a;
+                sb = b;
+            }
+        }
+        for (int o = 16; o; o >>= 1) {   // largest remaining range over the warp
+            const long long r2 = __shfl_xor_sync(kFull, best_rem, o);
+            const int i2 = __shfl_xor_sync(kFull, best, o);
+            const unsigned long long a2 = __shfl_xor_sync(kFull, sa, o);
+            const unsigned long long b2 = __shfl_xor_sync(kFull, sb, o);
+            if (r2 > best_rem || (r2 == best_rem && i2 > best)) {
+                best_rem = r2; best = i2; sa = a2; sb = b2;
+            }
+        }
+        if (best_rem < kStealMin) {
+            if (full) return;
+            full = true;   // nothing in this window: look at all slots once
+            continue;
+        }
+        full = nslots <= kStealWindow;
+        const long long cur = (long long)(unsigned)sb, end = (long long)(sb >> 32);
+        const long long half = best_rem / 2;
+        const long long mid = cur + (half + kProofTile - 1) / kProofTile * kProofTile;
+        bool ok = false;
+        if (lane == 0) {
+            const StealSlot seen{sa, sb};
+            ok = same(atomicCAS(&slots[best], seen, StealSlot{sa, pack_range(cur, mid)}), seen);
+            if (ok) slot_start(mine, (long long)sa - 1, mid, end);
+        }
+        if (!__shfl_sync(kFull, ok, 0)) continue;
+        table_tile<CACHE>(g, (long long)sa - 1, TT, mid, end, mine, rep, err, wc, leaf, cache,
+                          sblk);
+    }
+}
+
 template <bool PERSIST, bool CACHE, class LeafFn>
 __global__ void __launch_bounds__(kTravThreads, kTableMinBlocks)
 k_table(DevScenes g, long long total_items, long long all_items, int TT,
-                        const int *rep, unsigned long long *work, unsigned long long *ctr,
-                        int *err)
+                        const int *rep, unsigned long long *work, StealSlot *slots,
+                        unsigned long long *ctr, int *err)
 {
     extern __shared__ int smem_blk[];
     WalkCounters wc;
@@ -565,8 +720,12 @@ k_table(DevScenes g, long long total_items, long long all_items, int TT,
     OccluderCache cache;
     const int lane = threadIdx.x & 31;
     int *sblk = CACHE ? smem_blk + (threadIdx.x >> 5) * kSampleSlots : nullptr;
+    StealSlot *mine = (PERSIST && slots)
+                          ? slots + (size_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)
+                          : nullptr;
     auto run = [&](long long it) {
-        if (it < total_items) table_tile<CACHE>(g, it, TT, rep, err, wc, leaf, cache, sblk);
+        if (it < total_items)
+            table_tile<CACHE>(g, it, TT, -1, -1, mine, rep, err, wc, leaf, cache, sblk);
         else los_item<CACHE>(g, it - total_items, err, wc, leaf, cache);
     };
     if (!PERSIST) {
@@ -580,6 +739,7 @@ k_table(DevScenes g, long long total_items, long long all_items, int TT,
             if ((long long)base >= all_items) break;
             run((long long)base);
         }
+        if (mine) steal_loop<CACHE>(g, TT, slots, mine, rep, err, wc, leaf, cache, sblk);
     }
     flush_counters(wc, ctr);
 }
@@ -656,10 +816,18 @@ static void launch_one(const DevScenes &g, long long items, long long all, int T
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
         int blocks = cfg.n_sm * (per_sm > 0 ? per_sm : 1);
         cudaMemsetAsync(work, 0, sizeof(unsigned long long), st);
-        kern<<<blocks, threads, smem, st>>>(g, items, all, TT, rep, work, ctr, err);
+        // one slot per warp of the grid (the context holds 64 per SM)
+        StealSlot *slots = nullptr;
+        const long long warps = (long long)blocks * cfg.warps_per_block;
+        if (cfg.steal && warps <= 64LL * cfg.n_sm) {
+            slots = static_cast<StealSlot *>(cfg.steal);
+            cudaMemsetAsync(slots, 0, sizeof(StealSlot) * (size_t)warps, st);
+        }
+        kern<<<blocks, threads, smem, st>>>(g, items, all, TT, rep, work, slots, ctr, err);
     } else {
         long long blocks = (all + cfg.warps_per_block - 1) / cfg.warps_per_block;
-        kern<<<(unsigned)blocks, threads, smem, st>>>(g, items, all, TT, rep, work, ctr, err);
+        kern<<<(unsigned)blocks, threads, smem, st>>>(g, items, all, TT, rep, work, nullptr, ctr,
+                                                      err);
     }
 }
 

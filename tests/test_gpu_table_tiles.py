@@ -64,8 +64,27 @@ def test_routes_match_oracle_for_every_tile(ctx, seed, s):
     rx = route(rng, 9000, 150, n)
     tx = route(rng, 9000, 1500, n) if seed % 2 else np.repeat(sc.tx[:1], n, axis=0)
     tab, los = oracle.table(sc.facets, s, tx, rx)
-    for tile in (4, 16, 64):
-        (T, L), _ = ivm.ivm_build_table(ctx, sc.facets, s, tx, rx, mode=ivm.IVM_MODE_FILTERED,
-                                        flags=FAST, tile=tile)
-        assert (to_np(T) == tab).all(), tile
-        assert (L.cpu().numpy() == los).all()
+    for tile in (4, 16, 64, 400):
+        for flags in (FAST, FAST | ivm.IVM_FLAG_NO_SPLIT):
+            (T, L), _ = ivm.ivm_build_table(ctx, sc.facets, s, tx, rx,
+                                            mode=ivm.IVM_MODE_FILTERED, flags=flags, tile=tile)
+            assert (to_np(T) == tab).all(), (tile, flags)
+            assert (L.cpu().numpy() == los).all()
+
+
+@pytest.mark.parametrize("tile", [16, 100, 1000, 10000])
+def test_lazy_splitting_gives_the_same_rows(ctx, tile):
+    """Idle warps take the back half of busy warps' snapshot ranges: with one
+    item per word (tile 10,000) nearly every row comes from a split range.
+    The rows equal those of the launch without splitting, and sampled rows
+    equal the oracle's."""
+    sc = sg.district()
+    s = sc.samples_per_side
+    (T0, L0), _ = ivm.ivm_build_table(ctx, sc.facets, s, sc.tx, sc.rx, mode=ivm.IVM_MODE_FILTERED,
+                                      flags=FAST | ivm.IVM_FLAG_NO_SPLIT, tile=128)
+    (T, L), _ = ivm.ivm_build_table(ctx, sc.facets, s, sc.tx, sc.rx, mode=ivm.IVM_MODE_FILTERED,
+                                    flags=FAST, tile=tile)
+    assert (to_np(T) == to_np(T0)).all() and (L.cpu().numpy() == L0.cpu().numpy()).all()
+    snaps = np.arange(0, sc.n_snap, 997)
+    tab, los = oracle.table(sc.facets, s, sc.tx, sc.rx, snaps=snaps)
+    assert (to_np(T)[snaps] == tab).all() and (L.cpu().numpy()[snaps] == los).all()

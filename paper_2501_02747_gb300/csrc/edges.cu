@@ -54,7 +54,7 @@ k_edge_table(DevScenes g, EdgeArgs a, int *err)
     WalkCounters wc;
     OccluderCache cache;
     cache.enter_scene(0);
-    typename std::conditional<FILTERED, FilteredLeaf, ExactLeaf>::type leaf;
+    typename std::conditional<FILTERED, FilteredLeafCall, ExactLeaf>::type leaf;
     const int G = 32 / s;
     const int gi = lane / s, smp = lane - gi * s;
     for (int q = 0; q < 32; q++) s_blk[warp][q][lane] = -1;

@@ -97,6 +97,41 @@ __device__ __forceinline__ bool facet_hit_filtered(const Seg &s, const Leaf &L, 
                         s.dx, s.dy, s.dz, packed);
 }
 
+// The same test out of line, for kernels whose hot loop holds several walks:
+// one copy of the test instead of one per walk keeps the code small enough
+// for the instruction cache when many warps run different parts of it.  A
+// register-only interface (coordinates in, flags out: bit 0 = hit, bit 1 =
+// an exact test was used, bit 2 = the filter was undecided) keeps the call
+// free of local-memory traffic.
+static __device__ __noinline__ int facet_hit_filtered_call(int px, int py, int pz, int dx,
+                                                           int dy, int dz, int ox, int oy, int oz,
+                                                           int ux, int uy, int uz, int vx, int vy,
+                                                           int vz, int nx, int ny, int nz,
+                                                           int dom)
+{
+    const Seg s = make_seg(px, py, pz, px + dx, py + dy, pz + dz);
+    Leaf L;
+    L.ox = ox; L.oy = oy; L.oz = oz; L.building = 0;
+    L.ux = ux; L.uy = uy; L.uz = uz; L.scene = 0;
+    L.vx = vx; L.vy = vy; L.vz = vz; L.dom = dom;
+    L.nx = nx; L.ny = ny; L.nz = nz; L.pad = 0;
+    WalkCounters wc;
+    const bool hit = facet_hit_filtered(s, L, wc);
+    return (int)hit | ((wc.exact != 0) << 1) | ((wc.undecided != 0) << 2);
+}
+
+struct FilteredLeafCall {
+    __device__ __forceinline__ bool operator()(const Seg &s, const Leaf &L, WalkCounters &wc) const
+    {
+        const int r = facet_hit_filtered_call(s.px, s.py, s.pz, s.dx, s.dy, s.dz, L.ox, L.oy,
+                                              L.oz, L.ux, L.uy, L.uz, L.vx, L.vy, L.vz, L.nx,
+                                              L.ny, L.nz, L.dom);
+        wc.exact += (r >> 1) & 1;
+        wc.undecided += (r >> 2) & 1;
+        return r & 1;
+    }
+};
+
 struct FilteredLeaf {
     __device__ __forceinline__ bool operator()(const Seg &s, const Leaf &L, WalkCounters &wc) const
     {

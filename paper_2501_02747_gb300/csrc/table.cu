@@ -861,7 +861,7 @@ cudaError_t launch_table(const DevScenes &g, long long total_snap, long long tot
     if (cfg.mode == IVM_MODE_EXACT)
         launch_leaf<ExactLeaf>(g, total_items, all, snap_tile, cfg, r, work, ctr, err, st);
     else
-        launch_leaf<FilteredLeaf>(g, total_items, all, snap_tile, cfg, r, work, ctr, err, st);
+        launch_leaf<FilteredLeafCall>(g, total_items, all, snap_tile, cfg, r, work, ctr, err, st);
     if (cfg.dedup && total_snap > 0) {
         long long warps = 2 * total_snap;
         k_copy_rows<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, st>>>(g, total_snap, rep, ctr);

@@ -6,7 +6,7 @@
 // bounds, tested conservatively.
 //
 // Build: per-scene bounds of the facet centroids -> 30-bit Morton code per
-// facet -> sort keys (Morton << 32 | local index, unique) -> binary radix
+// facet (one cubic grid over the bounds) -> sort keys (Morton << 32 | local index, unique) -> binary radix
 // tree over the sorted keys (each internal node finds its key range and split
 // from common-prefix lengths, after T. Karras, "Maximizing parallelism in the
 // construction of BVHs, octrees, and k-d trees", HPG 2012) -> bottom-up box
@@ -58,11 +58,16 @@ __global__ void k_morton(DevScenes g, const int *bounds)
     const int sc = g.fscene[f];
     const int *b = g.box + 6 * (size_t)f;
     const int *B = bounds + 6 * sc;
+    // One scale for all three axes (the largest centroid span): a city is far
+    // wider than it is tall, and stretching each axis to its own span would
+    // give a few metres of height as many Morton levels as a kilometre of
+    // ground, scattering neighbours along the curve.
+    long long span = 0;
+    for (int a = 0; a < 3; a++) span = max(span, (long long)B[3 + a] - B[a]);
     unsigned q[3];
     for (int a = 0; a < 3; a++) {
         long long c = (long long)b[a] + b[3 + a];
-        long long lo = B[a], span = (long long)B[3 + a] - lo;
-        q[a] = span > 0 ? (unsigned)(((c - lo) * 1023) / span) : 0u;
+        q[a] = span > 0 ? (unsigned)(((c - B[a]) * 1023) / span) : 0u;
     }
     unsigned long long code = spread10(q[0]) | (spread10(q[1]) << 1) | (spread10(q[2]) << 2);
     // A facet spanning more than 1/4 of the scene in x or y (the ground) would

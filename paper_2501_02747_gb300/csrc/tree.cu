@@ -165,64 +165,87 @@ __global__ void k_init_runs(TreeArgs a, const long long *start, long long u0, in
 // For snapshots [t0, t1) (all in runs u0 .. u0 + C - 1): summary[t][k] =
 // sum_g x_k[c][g][run(t) - u0] vis_Rx[t][g] for k = 1..K, and order 0.
 // xs holds x_1 .. x_K, 3 n C words each.
+// Warp per snapshot: lanes take the Rx row's words, sum x over its set bits,
+// and the warp adds the lanes' sums (exact: arithmetic mod 2^64).
 __global__ void k_dot_runs(TreeArgs a, const int *run_of, long long t0, long long t1,
                            long long u0, int C, const unsigned long long *xs)
 {
-    const long long t = t0 + (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= t1) return;
+    const int lane = threadIdx.x & 31;
+    const long long t = t0 + (((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    if (t >= t1) return;   // uniform per warp
     const int ul = (int)(run_of[t] - u0);
     const size_t plane = (size_t)a.n * C;
     const uint32_t *rx = a.table + ((size_t)t * 2 + 1) * a.W;
     ivm_tree_summary *out = a.summary + (size_t)t * (a.K + 1);
-    const unsigned long long l = a.los[t] ? 1ull : 0ull;
-    out[0].count = l;
-    out[0].fp0 = l;
-    out[0].fp1 = l;
+    if (lane == 0) {
+        const unsigned long long l = a.los[t] ? 1ull : 0ull;
+        out[0].count = l;
+        out[0].fp0 = l;
+        out[0].fp1 = l;
+    }
     for (int k = 1; k <= a.K; k++) {
         const unsigned long long *x = xs + (size_t)(k - 1) * 3 * plane;
         unsigned long long s0 = 0, s1 = 0, s2 = 0;
-        for (int w = 0; w < a.W; w++) {
+        for (int w = lane; w < a.W; w += 32) {
             uint32_t word = rx[w];
             while (word) {
-                int b = __ffs(word) - 1;
+                const int b = __ffs(word) - 1;
                 word &= word - 1;
-                size_t o = (size_t)(32 * w + b) * C + ul;
+                const size_t o = (size_t)(32 * w + b) * C + ul;
                 s0 += x[o];
                 s1 += x[plane + o];
                 s2 += x[2 * plane + o];
             }
         }
-        out[k].count = s0;
-        out[k].fp0 = s1;
-        out[k].fp1 = s2;
+        for (int o = 16; o; o >>= 1) {
+            s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+            s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+            s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+        }
+        if (lane == 0) {
+            out[k].count = s0;
+            out[k].fp0 = s1;
+            out[k].fp1 = s2;
+        }
     }
 }
 
-// x_new[c][g][t] = w_c(k, g) * sum_{f in adj(g)} x_old[c][f][t]; warp = (g, 32 t)
-__global__ void k_hop(TreeArgs a, int C, int k, const unsigned long long *xo,
+// x_new[c][g][t] = w_c(k, g) * sum_{f in adj(g)} x_old[c][f][t].  Warp =
+// (row g, Cp consecutive runs t), Cp a power of two <= 32: lane = (group q,
+// run r), the 32 / Cp groups stride over the row's nonzeros and their sums
+// are added over the warp (exact: mod 2^64).  With few runs (a static
+// transmitter has one) the lanes still share the row's work.
+__global__ void k_hop(TreeArgs a, int C, int Cp, int k, const unsigned long long *xo,
                       unsigned long long *xn)
 {
     const int lane = threadIdx.x & 31;
     const long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int tiles = (C + 31) / 32;
+    const int tiles = (C + Cp - 1) / Cp;
     const long long g = wid / tiles;
-    if (g >= a.n) return;
-    const int tl = (int)(wid - g * tiles) * 32 + lane;
+    if (g >= a.n) return;   // uniform per warp
+    const int G = 32 / Cp;
+    const int r = lane & (Cp - 1), q = lane / Cp;
+    const int tl = (int)(wid - g * tiles) * Cp + r;
     const bool ok = tl < C;
     const size_t plane = (size_t)a.n * C;
     unsigned long long s0 = 0, s1 = 0, s2 = 0;
     const long long e = a.rowptr[g + 1];
-    for (long long p = a.rowptr[g]; p < e; p++) {
+    for (long long p = a.rowptr[g] + q; p < e; p += G) {
         const int f = __ldg(a.col + p);
         if (ok) {
-            size_t o = (size_t)f * C + tl;
+            const size_t o = (size_t)f * C + tl;
             s0 += xo[o];
             s1 += xo[plane + o];
             s2 += xo[2 * plane + o];
         }
     }
-    if (ok) {
-        size_t o = (size_t)g * C + tl;
+    for (int o = Cp; o < 32; o <<= 1) {
+        s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+        s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+        s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+    }
+    if (ok && q == 0) {
+        const size_t o = (size_t)g * C + tl;
         xn[o] = s0;
         xn[plane + o] = s1 * a.wt[(size_t)k * a.n + g];
         xn[2 * plane + o] = s2 * a.wt[(size_t)(a.K + 1) * a.n + (size_t)k * a.n + g];
@@ -385,11 +408,13 @@ cudaError_t tree_run_chunk(TreeArgs &a, const long long *start, const int *run_o
     const size_t block = (size_t)3 * a.n * C;
     dim3 gi((C + 127) / 128, a.n);
     k_init_runs<<<gi, 128, 0, st>>>(a, start, u0, C, xs);
-    const long long warps = (long long)a.n * ((C + 31) / 32);
+    int Cp = 1;
+    while (Cp < C && Cp < 32) Cp <<= 1;
+    const long long warps = (long long)a.n * ((C + Cp - 1) / Cp);
     for (int k = 2; k <= a.K; k++)
         k_hop<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, st>>>(
-            a, C, k, xs + (k - 2) * block, xs + (k - 1) * block);
-    k_dot_runs<<<(unsigned)((t1 - t0 + 127) / 128), 128, 0, st>>>(a, run_of, t0, t1, u0, C, xs);
+            a, C, Cp, k, xs + (k - 2) * block, xs + (k - 1) * block);
+    k_dot_runs<<<(unsigned)((t1 - t0 + 3) / 4), 128, 0, st>>>(a, run_of, t0, t1, u0, C, xs);
     note_launches(2 + (a.K - 1));
     return cudaGetLastError();
 }

@@ -62,7 +62,7 @@ constexpr bool kTableBatchProbe = true;
 constexpr bool kTableSampleBlockers = true;
 constexpr int kSampleSlots = 32 * 32;
 // Snapshots per straight-stretch proof (a work item may hold several).
-constexpr int kProofTile = 16;
+constexpr int kProofTile = 32;
 
 // ------------------------------------------------------------ lazy splitting
 
@@ -445,8 +445,9 @@ __device__ __noinline__ void table_tile(const DevScenes &g, long long item, int 
         }
         const long long u1 = min(u0 + (long long)kProofTile, t1);
         if (rep) {   // a stretch whose rows are all copied later needs nothing
-            const long long t = u0 + lane;
-            const bool traced = t < u1 && rep[2 * (D.snap0 + t) + side] == t;
+            bool traced = false;
+            for (long long t = u0 + lane; t < u1; t += 32)
+                traced |= rep[2 * (D.snap0 + t) + side] == t;
             if (!__any_sync(kFull, traced)) continue;
         }
         bool proof = CACHE && kTableTileProof && u1 - u0 >= 3 &&

@@ -549,6 +549,11 @@ def run_ours(args, ws, rank, local):
                        "ms_per_launch": kern_fast[dom] / args.steps,
                        "ms_per_step_matrix": kern_fast["matrix"] / args.steps,
                        "ms_per_step_table": kern_fast["table"] / args.steps}
+    # the same fraction against this GPU's measured FMA issue rate (eight
+    # independent FMA chains per thread, full occupancy: ivm_fp32_peak)
+    ffma = ivm.ivm_fp32_peak(ctx) / 1e12
+    out["roofline"]["peak_measured_ffma"] = ffma
+    out["roofline"]["frac_of_measured_ffma"] = achieved / ffma if ffma else None
 
     if not args.no_e2e:
         fac_h = torch.from_numpy(sc.facets).pin_memory()

@@ -271,6 +271,14 @@ int ivm_build_edge_table(ivm_ctx *ctx, const ivm_scene *scene, const ivm_params 
                          const int32_t *edges, int32_t n_edges, const int32_t *tx,
                          const int32_t *rx, int64_t n_snap, uint32_t *table, int32_t *nearest);
 
+/* Measured FP32 FMA issue rate of the context's GPU, in FMA lane operations
+ * per second (one per lane per FMA; FLOP/s is twice this): eight independent
+ * FMA chains per thread on a full-occupancy grid, best of three timed runs
+ * after one warm-up.  The denominator of the traversal kernels' "alu"
+ * roofline, which no library GEMM peak measures.  Errors: IVM_ERR_ARG,
+ * IVM_ERR_CUDA. */
+int ivm_fp32_peak(ivm_ctx *ctx, double *lane_ops_per_s);
+
 /* Edges as rows and columns of the matrix (Sec. I-II: per face or edge, the
  * visible faces and edges; the nodes of first-order diffraction, Sec. III-B).
  * Edge e is edges[6e..6e+5] as above, with s samples, and edge_faces[2e],

@@ -38,6 +38,7 @@ enum Slot {
     S_T_CNT, S_T_OFF, S_T_BS, S_T_BO, S_T_PATHS, S_T_FLAG, S_T_EXCL, S_T_RUN, S_T_START,
     S_TUNE_M, S_TUNE_T, S_TUNE_L,
     S_REL_M, S_REL_DEG, S_REL_OFF, S_REL_BS, S_REL_BO, S_REL_PAIRS, S_REL_REL, S_REL_RNG,
+    S_PEAK,
     S_EM_EDGES, S_EM_FACES, S_EM_FE, S_EM_EE, S_EM_WORK,
     S_EDGES, S_EDGE_TAB, S_EDGE_KEY, S_EDGE_NEAR,
     S_RAY_PATHS, S_RAY_VALID,
@@ -896,6 +897,17 @@ extern "C" int ivm_build_edge_table(ivm_ctx *c, const ivm_scene *scene, const iv
     if (n_host)
         CK(cudaMemcpyAsync(nearest, a.nearest, sizeof(int) * 2 * S, cudaMemcpyDeviceToHost,
                            c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return IVM_OK;
+}
+
+extern "C" int ivm_fp32_peak(ivm_ctx *c, double *lane_ops_per_s)
+{
+    if (!c || !lane_ops_per_s) return IVM_ERR_ARG;
+    DeviceGuard dg(c->device);
+    int r;
+    if ((r = ensure(c, S_PEAK, sizeof(float)))) return r;
+    CK(ffma_peak(c->n_sm, ptr<float>(c, S_PEAK), c->stream, lane_ops_per_s));
     CK(cudaStreamSynchronize(c->stream));
     return IVM_OK;
 }

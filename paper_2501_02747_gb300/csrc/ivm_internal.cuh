@@ -135,6 +135,9 @@ struct LaunchCfg {
     void *steal = nullptr;// table, persistent: 16-byte slots, 64 per SM (nullptr: no splitting)
 };
 
+// Measured FP32 FMA lane operations per second (peak.cu).
+cudaError_t ffma_peak(int n_sm, float *sink, cudaStream_t st, double *lane_ops_per_s);
+
 cudaError_t launch_matrix(const DevScenes &g, const int2 *pairs, unsigned long long npairs,
                           const LaunchCfg &cfg, unsigned long long *work,
                           unsigned long long *ctr, int *err, cudaStream_t st);

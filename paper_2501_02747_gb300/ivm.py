@@ -87,6 +87,7 @@ SIGNATURES = {
                                ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(_VP),
                                ctypes.POINTER(ivm_stats)], ctypes.c_int),
     "ivm_set_walk_budget": ([_VP, ctypes.c_int32], ctypes.c_int),
+    "ivm_fp32_peak": ([_VP, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     "ivm_build_edge_matrix": ([_VP, ctypes.POINTER(ivm_scene), ctypes.POINTER(ivm_params), _VP,
                                _VP, ctypes.c_int32, _VP, _VP], ctypes.c_int),
     "ivm_interface_relations": ([_VP, ctypes.POINTER(ivm_scene), ctypes.POINTER(ivm_params), _VP,
@@ -372,6 +373,13 @@ def ivm_build_matrix_rows(ctx, facets, s, rows, mode=IVM_MODE_EXACT, flags=0, ti
     _check(lib().ivm_build_matrix_rows(ctx.handle, scenes, len(flist), ctypes.byref(p), begin,
                                        end, ptrs, ctypes.byref(st)), "ivm_build_matrix_rows")
     return (out[0] if single else out), st
+
+
+def ivm_fp32_peak(ctx):
+    """Measured FP32 FMA lane operations per second of the context's GPU."""
+    v = ctypes.c_double(0.0)
+    _check(lib().ivm_fp32_peak(ctx.handle, ctypes.byref(v)), "ivm_fp32_peak")
+    return v.value
 
 
 def ivm_build_edge_matrix(ctx, facets, s, edges, edge_faces, mode=IVM_MODE_FILTERED, out=None):

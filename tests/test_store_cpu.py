@@ -29,3 +29,34 @@ def test_digest_depends_on_every_facet_and_s():
     assert store.scene_digest(sc.facets[:-1], 3) != d0
     assert store.scene_digest(sc.facets[::-1], 3) != d0
     assert store.scene_digest(sc.facets, 4) != d0
+
+
+def test_table_chunks_resume(tmp_path):
+    """Chunked tables equal the one-shot table; a stopped run resumes at the
+    missing chunks only, and a chunk is rebuilt when its positions change or
+    its file is damaged."""
+    sc = sg.tiny()
+    s = 2
+    full_t, full_l = oracle.table(sc.facets, s, sc.tx, sc.rx)
+    calls = []
+
+    def build(a, b):
+        calls.append((a, b))
+        return oracle.table(sc.facets, s, sc.tx[a:b], sc.rx[a:b])
+
+    d = tmp_path / "chunks"
+    T, L, built, loaded = store.build_table_resumable(build, sc.facets, s, sc.tx, sc.rx, d, 32)
+    assert (T == full_t).all() and (L == full_l).all() and (built, loaded) == (4, 0)
+    calls.clear()
+    (d / "table_0000000032_0000000064.npz").unlink()                  # a run that stopped there
+    (d / "table_0000000064_0000000096.npz").write_bytes(b"half written")
+    T, L, built, loaded = store.build_table_resumable(build, sc.facets, s, sc.tx, sc.rx, d, 32)
+    assert (T == full_t).all() and (L == full_l).all()
+    assert calls == [(32, 64), (64, 96)] and (built, loaded) == (2, 2)
+    rx2 = sc.rx.copy()
+    rx2[70, 0] += 5                                                   # one position of chunk 2 moved
+    calls.clear()
+    T, L, built, loaded = store.build_table_resumable(build, sc.facets, s, sc.tx, rx2, d, 32)
+    want_t, want_l = oracle.table(sc.facets, s, sc.tx, rx2)
+    assert calls == [(64, 96)] and (T == want_t).all() and (L == want_l).all()
+    assert not list(d.glob("*.tmp"))

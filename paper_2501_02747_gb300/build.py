@@ -41,7 +41,10 @@ def _digest() -> str:
         for f in sorted(os.listdir(d)):
             with open(os.path.join(d, f), "rb") as fh:
                 h.update(f.encode() + fh.read())
-    h.update(" ".join(ARCH + FLAGS).encode())
+    # the include directories by name only: the digest must not depend on where
+    # the tree sits (profiles record it for the sources, on any machine)
+    flags = [os.path.basename(f) if f in (INCLUDE, CSRC) else f for f in FLAGS]
+    h.update(" ".join(ARCH + flags).encode())
     return h.hexdigest()
 
 

@@ -296,6 +296,40 @@ def test_district_table_full_size(district_gpu):
     assert (oracle.los_entries(sc.facets, 5, sc.tx[ts2], sc.rx[ts2]) == L[ts2]).all()
 
 
+def test_district_in_the_bench_launch_configuration(ctx, district_gpu):
+    """The configuration the benchmark times: autotuned launch shapes, device
+    buffers and graph replay (a capture, then a replay) of all three calls.
+    Matrix, table and LoS equal the plain form's (which the full-size tests
+    above check against the oracle), and so do the image-tree summaries."""
+    import torch
+    sc, M, Mf, T, L, Tf, Lf, st = district_gpu
+    n, S, K = sc.n_facets, sc.n_snap, sc.max_order
+    F = torch.from_numpy(sc.facets).cuda()
+    tx = torch.from_numpy(sc.tx).cuda()
+    rx = torch.from_numpy(sc.rx).cuda()
+    flags = FAST | ivm.IVM_FLAG_GRAPH
+    tuned = ivm.ivm_autotune(ctx, F, 5, tx, rx, mode=ivm.IVM_MODE_FILTERED, flags=flags)
+    W = (n + 31) // 32
+    Md = torch.empty((n, W), dtype=torch.int32, device="cuda")
+    Td = torch.empty((S, 2, W), dtype=torch.int32, device="cuda")
+    Ld = torch.empty((S,), dtype=torch.uint8, device="cuda")
+    Sd = torch.empty((S, K + 1, 3), dtype=torch.int64, device="cuda")
+    for _ in range(2):   # capture, then replay
+        ivm.ivm_build_matrix(ctx, F, 5, mode=ivm.IVM_MODE_FILTERED, flags=flags,
+                             tile=tuned["tile"], warps_per_block=tuned["warps_per_block"], out=Md)
+        ivm.ivm_build_table(ctx, F, 5, tx, rx, mode=ivm.IVM_MODE_FILTERED, flags=flags,
+                            tile=tuned["table_tile"], warps_per_block=tuned["warps_per_block"],
+                            out=(Td, Ld))
+        ivm.ivm_expand_image_tree(ctx, Md, Td, Ld, n, K, summary=Sd)
+        torch.cuda.synchronize()
+        assert (to_np(Md) == M).all()
+        assert (to_np(Td) == T).all() and (Ld.cpu().numpy() == L).all()
+    want, _ = ivm.ivm_expand_image_tree(ctx, torch.from_numpy(M.view(np.int32)).cuda(),
+                                        torch.from_numpy(T.view(np.int32)).cuda(),
+                                        torch.from_numpy(L).cuda(), n, K)
+    assert (Sd.cpu().numpy() == want.cpu().numpy()).all()
+
+
 def test_degenerate_filtered_equals_exact_and_oracle(ctx):
     sc = sg.degenerate()
     n = sc.n_facets

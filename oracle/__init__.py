@@ -8,7 +8,10 @@ marshals numpy arrays.  Work is spread over threads by row / snapshot
 range; ctypes releases the GIL during each foreign call.
 
 The definition it computes, with the paper sections it follows, is in the
-header comment of ``ivm_oracle.c``.
+header comment of ``ivm_oracle.c``; the visibility ranges (run lengths of
+table bits), the interface relations and angular bouncing ranges (Table I,
+Eq. (1)-(2)) are computed here in numpy from exact integers, and the
+image-method ray validation in ``rays.py`` with exact fractions.
 """
 from __future__ import annotations
 

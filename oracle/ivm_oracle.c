@@ -44,13 +44,6 @@
  *  7. Traditional per-snapshot method [Sec. IV-B, brute-force image tree per
  *     location]: the same path sets with every hop's visibility recomputed
  *     from geometry at every snapshot, no cached matrix.
- *  9. Edges [Sec. I and II: the matrix lists visible faces and edges;
- *     Sec. III-B: first-order diffraction uses the edge closest to the
- *     receiver].  Edge e = segment A -> B (cm) has s samples at the cell
- *     centres p_a = 2s A + (2a+1)(B - A), a in [0, s).  vis_X[t][e] = some
- *     sample p_a has not blocked(X_t, p_a); the nearest visible edge of X_t is
- *     the visible edge with the sample closest to X_t (squared distance over
- *     all of its samples, ties to the lower edge index), -1 if none.
  *  8. Blockage [Sec. III-C, Tables III-IV, "Blockage" column]: the first
  *     facet the segment from a source point to facet j's centre sample
  *     (a = b = floor(s/2)) meets, i.e. the hit with the smallest parameter l
@@ -58,6 +51,20 @@
  *     inside a coplanar facet); ties go to the lower facet index.  The
  *     visibility ranges themselves (runs of a table bit along the route,
  *     Tables III-IV) are read off the table in oracle/__init__.py.
+ *  9. Edges [Sec. I and II: the matrix lists visible faces and edges;
+ *     Sec. III-B: first-order diffraction uses the edge closest to the
+ *     receiver].  Edge e = segment A -> B (cm) has s samples at the cell
+ *     centres p_a = 2s A + (2a+1)(B - A), a in [0, s).  vis_X[t][e] = some
+ *     sample p_a has not blocked(X_t, p_a); the nearest visible edge of X_t is
+ *     the visible edge with the sample closest to X_t (squared distance over
+ *     all of its samples, ties to the lower edge index), -1 if none.
+ * 10. Edges as rows and columns of the matrix [Sec. I and II: per face or
+ *     edge, the visible faces and edges].  Edge e also names the two facets
+ *     meeting at it; a point reaches e from outside its building only when it
+ *     is strictly in front of one of them (ext).  fe[i][e]: some sample p of
+ *     facet i and sample q of e with front(q, i), ext(p, e) and not
+ *     blocked(p, q); ee[e][g]: e != g and samples q of e, r of g with
+ *     ext(r, e), ext(q, g) and not blocked(q, r).
  *
  * Bit layout of rows: bit j of a row is word j >> 5, bit j & 31 (LSB first);
  * W = ceil(N / 32) words per row; padding bits are 0.

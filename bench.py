@@ -103,7 +103,7 @@ class Clocks:
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.fh,
+                 "--format=csv,noheader,nounits", "-lms", "25"], stdout=self.fh,
                 stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
@@ -125,12 +125,20 @@ class Clocks:
         except Exception:
             self.proc.kill()
         self.fh.close()
+        with open(self.path) as fh:
+            lines = fh.readlines()
+        os.unlink(self.path)
+        return Clocks.summarize(lines)
+
+    @staticmethod
+    def summarize(lines):
+        """Median SM clock, the highest max clock and the throttle reasons seen
+        in nvidia-smi's CSV lines (the FIELDS order, no header, no units)."""
         rows = []
-        for line in open(self.path):
+        for line in lines:
             f = [x.strip() for x in line.split(",")]
             if len(f) >= 9:
                 rows.append(f)
-        os.unlink(self.path)
         if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
         sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]

@@ -97,6 +97,15 @@ def lib():
                                               ctypes.c_int32, _u32p, ctypes.c_int32,
                                               ctypes.c_int32, _u32p]
         L.oracle_edge_matrix_rows.restype = None
+        L.oracle_matrix_rows_grid.argtypes = [_i32p, ctypes.c_int32, ctypes.c_int32, _i32p,
+                                              ctypes.c_int32, _u32p]
+        L.oracle_matrix_rows_grid.restype = None
+        L.oracle_table_grid.argtypes = [_i32p, ctypes.c_int32, ctypes.c_int32, _i32p, _i32p,
+                                        _i64p, ctypes.c_int64, _u32p, _u8p]
+        L.oracle_table_grid.restype = None
+        L.oracle_grid_candidates.argtypes = [_i32p, ctypes.c_int32, ctypes.c_int32, _i64p, _i64p,
+                                             _u8p]
+        L.oracle_grid_candidates.restype = None
         _lib = L
     return _lib
 
@@ -127,6 +136,18 @@ def blocked(facets, s, P, Q) -> bool:
     P = np.ascontiguousarray(P, dtype=np.int64)
     Q = np.ascontiguousarray(Q, dtype=np.int64)
     return bool(lib().oracle_blocked(_p(F, _i32p), F.shape[0], s, _p(P, _i64p), _p(Q, _i64p)))
+
+
+def grid_candidates(facets, s, P, Q) -> np.ndarray:
+    """Triangles (2 * facet + t) the grid mode tests for the segment P-Q
+    (scaled points): bool [2 N]."""
+    F = _facets(facets)
+    P = np.ascontiguousarray(P, dtype=np.int64)
+    Q = np.ascontiguousarray(Q, dtype=np.int64)
+    marks = np.zeros(2 * F.shape[0], dtype=np.uint8)
+    lib().oracle_grid_candidates(_p(F, _i32p), F.shape[0], s, _p(P, _i64p), _p(Q, _i64p),
+                                 _p(marks, _u8p))
+    return marks.astype(bool)
 
 
 def pair_free_count(facets, s, i, j) -> int:
@@ -174,13 +195,37 @@ def los_entries(facets, s, A, B, threads=None) -> np.ndarray:
     return np.asarray(out, dtype=np.uint8)
 
 
-def matrix(facets, s, rows=None, threads=None) -> np.ndarray:
-    """Matrix rows (all rows by default): uint32 [len(rows)][W]."""
+def _chunks(count, threads, per=4):
+    """Index ranges splitting `count` items into about `per` chunks per thread."""
+    step = max(1, -(-count // (per * _threads(threads))))
+    return [(a, min(count, a + step)) for a in range(0, count, step)]
+
+
+def matrix(facets, s, rows=None, threads=None, mode="brute") -> np.ndarray:
+    """Matrix rows (all rows by default): uint32 [len(rows)][W].
+
+    mode "brute" tests every segment against every triangle; "grid" decides
+    the same entries with candidates from an exact xy grid (step 11 of
+    ivm_oracle.c), for scenes too large for brute force."""
     F = _facets(facets)
     n = F.shape[0]
     rows = np.arange(n) if rows is None else np.asarray(rows, dtype=np.int64)
     out = np.zeros((len(rows), words(n)), dtype=np.uint32)
     L = lib()
+    if mode == "grid":
+        r32 = np.ascontiguousarray(rows, dtype=np.int32)
+
+        def chunk(ab):
+            a, b = ab
+            if b > a:
+                L.oracle_matrix_rows_grid(_p(F, _i32p), n, s, _p(r32[a:b], _i32p), b - a,
+                                          _p(out[a:b], _u32p))
+
+        with ThreadPoolExecutor(_threads(threads)) as ex:
+            list(ex.map(chunk, _chunks(len(rows), threads)))
+        return out
+    if mode != "brute":
+        raise ValueError(f"unknown oracle mode {mode!r}")
 
     def one(k):
         r = int(rows[k])
@@ -191,16 +236,31 @@ def matrix(facets, s, rows=None, threads=None) -> np.ndarray:
     return out
 
 
-def table(facets, s, tx, rx, snaps=None, threads=None):
-    """Table rows for the given snapshots: (uint32 [n][2][W], uint8 [n])."""
+def table(facets, s, tx, rx, snaps=None, threads=None, mode="brute"):
+    """Table rows for the given snapshots: (uint32 [n][2][W], uint8 [n]).
+    mode as for matrix()."""
     F = _facets(facets)
     n = F.shape[0]
     tx = np.ascontiguousarray(tx, dtype=np.int32).reshape(-1, 3)
     rx = np.ascontiguousarray(rx, dtype=np.int32).reshape(-1, 3)
     snaps = np.arange(tx.shape[0]) if snaps is None else np.asarray(snaps, dtype=np.int64)
+    snaps = np.ascontiguousarray(snaps, dtype=np.int64)
     tab = np.zeros((len(snaps), 2, words(n)), dtype=np.uint32)
     los = np.zeros(len(snaps), dtype=np.uint8)
     L = lib()
+    if mode == "grid":
+        def chunk(ab):
+            a, b = ab
+            if b > a:
+                L.oracle_table_grid(_p(F, _i32p), n, s, _p(tx, _i32p), _p(rx, _i32p),
+                                    _p(snaps[a:b], _i64p), b - a, _p(tab[a:b], _u32p),
+                                    _p(los[a:b], _u8p))
+
+        with ThreadPoolExecutor(_threads(threads)) as ex:
+            list(ex.map(chunk, _chunks(len(snaps), threads)))
+        return tab, los
+    if mode != "brute":
+        raise ValueError(f"unknown oracle mode {mode!r}")
 
     def one(k):
         t = int(snaps[k])

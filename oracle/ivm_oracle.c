@@ -66,6 +66,13 @@
  *     blocked(p, q); ee[e][g]: e != g and samples q of e, r of g with
  *     ext(r, e), ext(q, g) and not blocked(q, r).
  *
+ * 11. Grid mode.  The same matrix and table entries, each decided by the
+ *     same triangle test on the same triangles; a segment is only tested
+ *     against the triangles an exact xy grid cannot rule out (see the grid
+ *     section below for why no hit is missed).  It is the reference for
+ *     scenes too large for brute force and is checked bit for bit against
+ *     brute force on smaller ones.
+ *
  * Bit layout of rows: bit j of a row is word j >> 5, bit j & 31 (LSB first);
  * W = ceil(N / 32) words per row; padding bits are 0.
  */
@@ -520,6 +527,282 @@ OR_EXPORT void oracle_table(const int32_t *facets, int32_t n, int32_t s, const i
                     row[side * W + (j >> 5)] |= 1u << (j & 31);
         los[t - t0] = (uint8_t)!blocked(F, n, X[0], X[1]);
     }
+    free(F);
+}
+
+/* ------------------------------------------ grid mode: the same definition
+ *
+ * The full-size reference for scenes too large for brute force.  It decides
+ * exactly what blocked(), pair_visible() and point_sees() decide, with the
+ * same seg_hits_tri() on the same triangles; only the set of triangles a
+ * segment is tested against is narrowed first, to those that can possibly
+ * meet it:
+ *
+ *  - An xy grid of nx * ny square cells of width w (scaled units) covers the
+ *    scene.  Cell (cx, cy) holds every triangle whose closed xy bounding box
+ *    meets the cell's column cx and row cy, where the column of a coordinate
+ *    x is floor((x - gx0) / w) clamped to [0, nx - 1] (rows alike).
+ *  - A segment visits, column by column, every cell the column's part of
+ *    the closed segment can lie in: for column c the part has x in [xa, xb]
+ *    (xa = the segment's smallest x in its first column, else the column's
+ *    left edge; xb alike), so y lies between y(xa) and y(xb), and the rows
+ *    from cell(min) to cell(max) are visited.  y(x) is a fraction of
+ *    integers and is floored exactly.
+ *  - Why nothing is missed: a point X where the segment meets a triangle
+ *    lies in that triangle's bounding box, so its cell holds the triangle;
+ *    X lies on the segment, in column cell(X.x), between that column's xa
+ *    and xb, so its row is among those visited.
+ *  - Each triangle is tested once per segment (a per-call stamp), and only
+ *    if its 3D bounding box meets the segment's (a disjoint box cannot hold
+ *    a point of the segment).
+ */
+
+typedef struct {
+    const Facet *F;
+    int32_t n_tri;
+    i128 gx0, gy0, w;
+    int32_t nx, ny;
+    int32_t *start;        /* nx * ny + 1 offsets into ids */
+    int32_t *ids;          /* triangle ids: 2 * facet + t */
+    i128 (*box)[6];        /* per triangle: min x, y, z, max x, y, z */
+    uint32_t *stamp;
+    uint32_t epoch;
+} Grid;
+
+static i128 floordiv(i128 a, i128 b)   /* b > 0 */
+{
+    i128 q = a / b;
+    if ((a % b != 0) && (a < 0)) q -= 1;
+    return q;
+}
+
+static int32_t cell_of(i128 x, i128 x0, i128 w, int32_t m)
+{
+    i128 c = floordiv(x - x0, w);
+    if (c < 0) c = 0;
+    if (c > m - 1) c = m - 1;
+    return (int32_t)c;
+}
+
+static i128 min3(i128 a, i128 b, i128 c) { i128 m = a < b ? a : b; return m < c ? m : c; }
+static i128 max3(i128 a, i128 b, i128 c) { i128 m = a > b ? a : b; return m > c ? m : c; }
+
+static void grid_build(Grid *g, const Facet *F, int32_t n)
+{
+    memset(g, 0, sizeof *g);
+    g->F = F;
+    g->n_tri = 2 * n;
+    g->box = malloc(sizeof(i128[6]) * (size_t)(g->n_tri > 0 ? g->n_tri : 1));
+    i128 lo[2] = {0, 0}, hi[2] = {0, 0};
+    for (int32_t k = 0; k < g->n_tri; k++) {
+        const V *T = F[k / 2].tri[k % 2];
+        i128 *b = g->box[k];
+        b[0] = min3(T[0].x, T[1].x, T[2].x); b[3] = max3(T[0].x, T[1].x, T[2].x);
+        b[1] = min3(T[0].y, T[1].y, T[2].y); b[4] = max3(T[0].y, T[1].y, T[2].y);
+        b[2] = min3(T[0].z, T[1].z, T[2].z); b[5] = max3(T[0].z, T[1].z, T[2].z);
+        for (int a = 0; a < 2; a++) {
+            if (k == 0 || b[a] < lo[a]) lo[a] = b[a];
+            if (k == 0 || b[3 + a] > hi[a]) hi[a] = b[3 + a];
+        }
+    }
+    /* about one cell per facet, at most 1024 per axis */
+    int32_t m = 1;
+    while ((int64_t)m * m < n && m < 1024) m++;
+    i128 span = hi[0] - lo[0] > hi[1] - lo[1] ? hi[0] - lo[0] : hi[1] - lo[1];
+    g->w = span / m + 1;
+    g->gx0 = lo[0];
+    g->gy0 = lo[1];
+    g->nx = g->ny = m;
+    int32_t nc = g->nx * g->ny;
+    g->start = calloc((size_t)nc + 1, sizeof(int32_t));
+    for (int pass = 0; pass < 2; pass++) {
+        int32_t *fill = pass ? calloc((size_t)nc, sizeof(int32_t)) : NULL;
+        for (int32_t k = 0; k < g->n_tri; k++) {
+            const i128 *b = g->box[k];
+            int32_t c0 = cell_of(b[0], g->gx0, g->w, g->nx), c1 = cell_of(b[3], g->gx0, g->w, g->nx);
+            int32_t r0 = cell_of(b[1], g->gy0, g->w, g->ny), r1 = cell_of(b[4], g->gy0, g->w, g->ny);
+            for (int32_t c = c0; c <= c1; c++)
+                for (int32_t r = r0; r <= r1; r++) {
+                    int32_t cell = c * g->ny + r;
+                    if (pass == 0) g->start[cell + 1]++;
+                    else g->ids[g->start[cell] + fill[cell]++] = k;
+                }
+        }
+        if (pass == 0) {
+            for (int32_t c = 0; c < nc; c++) g->start[c + 1] += g->start[c];
+            g->ids = malloc(sizeof(int32_t) * (size_t)(g->start[nc] > 0 ? g->start[nc] : 1));
+        } else {
+            free(fill);
+        }
+    }
+    g->stamp = calloc((size_t)(g->n_tri > 0 ? g->n_tri : 1), sizeof(uint32_t));
+}
+
+static void grid_free(Grid *g)
+{
+    free(g->start); free(g->ids); free(g->box); free(g->stamp);
+}
+
+/* Calls visit(g, k, P, Q, arg) for every candidate triangle k of the closed
+ * segment PQ (each once), in columns and rows ordered from P towards Q;
+ * stops when visit returns nonzero and returns that value. */
+typedef int (*grid_visit)(Grid *g, int32_t k, V P, V Q, void *arg);
+
+static int grid_walk(Grid *g, V P, V Q, grid_visit visit, void *arg)
+{
+    if (++g->epoch == 0) {                     /* stamps wrapped: start over */
+        memset(g->stamp, 0, sizeof(uint32_t) * (size_t)g->n_tri);
+        g->epoch = 1;
+    }
+    i128 sb[6] = {P.x < Q.x ? P.x : Q.x, P.y < Q.y ? P.y : Q.y, P.z < Q.z ? P.z : Q.z,
+                  P.x > Q.x ? P.x : Q.x, P.y > Q.y ? P.y : Q.y, P.z > Q.z ? P.z : Q.z};
+    i128 dx = Q.x - P.x, dy = Q.y - P.y;
+    int32_t cP = cell_of(P.x, g->gx0, g->w, g->nx), cQ = cell_of(Q.x, g->gx0, g->w, g->nx);
+    int32_t c0 = cP < cQ ? cP : cQ, c1 = cP < cQ ? cQ : cP;
+    int cstep = cP <= cQ ? 1 : -1;
+    for (int32_t c = cP;; c += cstep) {
+        i128 xa = (c == c0) ? sb[0] : g->gx0 + (i128)c * g->w;
+        i128 xb = (c == c1) ? sb[3] : g->gx0 + (i128)(c + 1) * g->w;
+        int32_t r0, r1;
+        if (dx == 0) {
+            r0 = cell_of(sb[1], g->gy0, g->w, g->ny);
+            r1 = cell_of(sb[4], g->gy0, g->w, g->ny);
+        } else {
+            /* y(x) = P.y + (x - P.x) dy / dx = num / den, den > 0 */
+            i128 den = dx > 0 ? dx : -dx, sg = dx > 0 ? 1 : -1;
+            i128 na = sg * (P.y * dx + (xa - P.x) * dy), nb = sg * (P.y * dx + (xb - P.x) * dy);
+            i128 nlo = na < nb ? na : nb, nhi = na < nb ? nb : na;
+            /* row of y = floor((y - gy0) / w) = floor((num - gy0 den) / (w den)) */
+            i128 rl = floordiv(nlo - g->gy0 * den, g->w * den);
+            i128 rh = floordiv(nhi - g->gy0 * den, g->w * den);
+            if (rl < 0) rl = 0;
+            if (rl > g->ny - 1) rl = g->ny - 1;
+            if (rh < 0) rh = 0;
+            if (rh > g->ny - 1) rh = g->ny - 1;
+            r0 = (int32_t)rl;
+            r1 = (int32_t)rh;
+        }
+        int rstep = dy >= 0 ? 1 : -1;
+        int32_t rs = rstep > 0 ? r0 : r1, re = rstep > 0 ? r1 : r0;
+        for (int32_t r = rs;; r += rstep) {
+            int32_t cell = c * g->ny + r;
+            for (int32_t q = g->start[cell]; q < g->start[cell + 1]; q++) {
+                int32_t k = g->ids[q];
+                if (g->stamp[k] == g->epoch) continue;
+                g->stamp[k] = g->epoch;
+                const i128 *b = g->box[k];
+                if (b[0] > sb[3] || b[3] < sb[0] || b[1] > sb[4] || b[4] < sb[1] ||
+                    b[2] > sb[5] || b[5] < sb[2])
+                    continue;
+                int v = visit(g, k, P, Q, arg);
+                if (v) return v;
+            }
+            if (r == re) break;
+        }
+        if (c == cQ) break;
+    }
+    return 0;
+}
+
+static int visit_hit(Grid *g, int32_t k, V P, V Q, void *arg)
+{
+    const V *T = g->F[k / 2].tri[k % 2];
+    return seg_hits_tri(P, Q, T[0], T[1], T[2]);
+}
+
+/* blocked() with the candidates of the grid */
+static int blocked_grid(Grid *g, V P, V Q) { return grid_walk(g, P, Q, visit_hit, NULL); }
+
+static int pair_visible_grid(Grid *g, int s, int32_t i, int32_t j)
+{
+    const Facet *F = g->F;
+    if (i == j) return 0;
+    for (int a0 = 0; a0 < s; a0++)
+        for (int a1 = 0; a1 < s; a1++) {
+            V p = sample(&F[i], s, a0, a1);
+            if (!front(p, &F[j])) continue;
+            for (int b0 = 0; b0 < s; b0++)
+                for (int b1 = 0; b1 < s; b1++) {
+                    V q = sample(&F[j], s, b0, b1);
+                    if (!front(q, &F[i])) continue;
+                    if (!blocked_grid(g, p, q)) return 1;
+                }
+        }
+    return 0;
+}
+
+static int point_sees_grid(Grid *g, int s, V X, int32_t j)
+{
+    const Facet *F = g->F;
+    if (!front(X, &F[j])) return 0;
+    for (int b0 = 0; b0 < s; b0++)
+        for (int b1 = 0; b1 < s; b1++)
+            if (!blocked_grid(g, X, sample(&F[j], s, b0, b1))) return 1;
+    return 0;
+}
+
+/* Grid mode of oracle_matrix_rows: the listed rows (n_rows of them), out is
+ * n_rows x W words. */
+OR_EXPORT void oracle_matrix_rows_grid(const int32_t *facets, int32_t n, int32_t s,
+                                       const int32_t *rows, int32_t n_rows, uint32_t *out)
+{
+    int32_t W = oracle_words(n);
+    Facet *F = load_facets(facets, n, s);
+    Grid g;
+    grid_build(&g, F, n);
+    memset(out, 0, sizeof(uint32_t) * (size_t)W * (size_t)n_rows);
+    for (int32_t k = 0; k < n_rows; k++) {
+        int32_t i = rows[k];
+        for (int32_t j = 0; j < n; j++)
+            if (pair_visible_grid(&g, s, i, j)) out[(size_t)k * W + (j >> 5)] |= 1u << (j & 31);
+    }
+    grid_free(&g);
+    free(F);
+}
+
+/* Grid mode of oracle_table: the listed snapshots, table is n_snaps x 2 x W,
+ * los is n_snaps bytes; tx, rx are the full [S][3] arrays (cm). */
+OR_EXPORT void oracle_table_grid(const int32_t *facets, int32_t n, int32_t s, const int32_t *tx,
+                                 const int32_t *rx, const int64_t *snaps, int64_t n_snaps,
+                                 uint32_t *table, uint8_t *los)
+{
+    int32_t W = oracle_words(n);
+    Facet *F = load_facets(facets, n, s);
+    Grid g;
+    grid_build(&g, F, n);
+    memset(table, 0, sizeof(uint32_t) * (size_t)W * 2 * (size_t)n_snaps);
+    for (int64_t k = 0; k < n_snaps; k++) {
+        int64_t t = snaps[k];
+        V X[2] = {point_of(tx + 3 * t, s), point_of(rx + 3 * t, s)};
+        uint32_t *row = table + (size_t)k * 2 * W;
+        for (int side = 0; side < 2; side++)
+            for (int32_t j = 0; j < n; j++)
+                if (point_sees_grid(&g, s, X[side], j))
+                    row[side * W + (j >> 5)] |= 1u << (j & 31);
+        los[k] = (uint8_t)!blocked_grid(&g, X[0], X[1]);
+    }
+    grid_free(&g);
+    free(F);
+}
+
+/* The grid's candidate set of the segment PQ (scaled points): marks[k] = 1
+ * for every triangle k = 2 * facet + t that grid_walk would test (before the
+ * 3D box check), for the test that the candidates cover every hit. */
+static int visit_mark(Grid *g, int32_t k, V P, V Q, void *arg)
+{
+    ((uint8_t *)arg)[k] = 1;
+    return 0;
+}
+
+OR_EXPORT void oracle_grid_candidates(const int32_t *facets, int32_t n, int32_t s,
+                                      const int64_t *P, const int64_t *Q, uint8_t *marks)
+{
+    Facet *F = load_facets(facets, n, s);
+    Grid g;
+    grid_build(&g, F, n);
+    memset(marks, 0, (size_t)2 * n);
+    grid_walk(&g, mk(P[0], P[1], P[2]), mk(Q[0], Q[1], Q[2]), visit_mark, marks);
+    grid_free(&g);
     free(F);
 }
 

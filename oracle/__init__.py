@@ -491,50 +491,88 @@ def interface_relations(facets, M, n_facets=None):
     [Sec. II-B, Table I, Eq. (1)-(2)].
 
     relation: 1 = PAR (normals parallel), 2 = PER (normals perpendicular),
-    0 = neither.  For edge k of face i (k = 0..3 along O -> O+U -> O+U+V ->
-    O+V), B_k is the edge's midpoint and the reference vector points from B_k
-    to the opposite edge's midpoint (the paper's BA, along the face); each
-    corner F of face j gives omega = arccos(ref . (F - B_k) / |ref| |F - B_k|)
-    in degrees (Eq. (1)), with omega = 180 recorded as 0 (Eq. (2)); the
-    edge's range is (min, max) over j's four corners.  float64; 180 degrees
-    (F - B_k opposite to the reference vector) is decided exactly on the
-    doubled integer vectors, so the Eq. (2) rule never hangs on rounding (an
-    angle just below 180 that rounds to 180.0 stays as computed).
+    0 = neither.
+
+    Angles.  The paper reads them in 2D views (the xy-plane and the xz- or
+    yz-plane), measured clockwise from a reference line, so that a value can
+    exceed 180 degrees; Eq. (2) records such values as 0.  For edge k of face
+    i (k = 0..3 along O -> O+U -> O+U+V -> O+V) the view is the plane through
+    the edge's midpoint B perpendicular to the edge (for box buildings: the
+    xy-plane for a vertical edge, the xz- or yz-plane for a horizontal one).
+    The reference line runs from B towards the opposite edge's midpoint (the
+    paper's BA, along the face), and the angle turns from it towards face i's
+    outward normal, the side from which the face can be seen.  A corner F of
+    face j, projected into the view (its component along the edge removed),
+    is at the angle theta in [0, 360):
+      * theta < 180 when the projection lies strictly on the outward side, or
+        in the face's plane along the reference line; then theta is Eq. (1),
+        arccos(ref . w / |ref| |w|), w the projected B -> F;
+      * theta >= 180 when it lies behind the face's plane, or in the plane
+        beyond the edge (exactly 180): recorded as 0 (Eq. (2));
+      * a corner on the edge's own line has no direction in the view: 0.
+    These cases are decided exactly on integers (doubled coordinates, so that
+    midpoints are integers); the value of Eq. (1) is float64.  The edge's
+    range is (min, max) over j's four corners.
     Returns (pairs int32 [P][2], relation uint8 [P], ranges float64 [P][4][2])."""
     F = _facets(facets)
     n = F.shape[0] if n_facets is None else n_facets
     bits = np.unpackbits(np.ascontiguousarray(M, dtype=np.uint32).view(np.uint8),
                          bitorder="little").reshape(n, -1)[:, :n]
     ii, jj = np.nonzero(bits)
-    O = F[:, 0:3].astype(np.float64)
-    U = F[:, 3:6].astype(np.float64)
-    V = F[:, 6:9].astype(np.float64)
-    Ni = np.cross(F[:, 3:6].astype(np.int64), F[:, 6:9].astype(np.int64))
     pairs = np.stack([ii, jj], axis=1).astype(np.int32)
     rel = np.zeros(len(ii), np.uint8)
     rng = np.zeros((len(ii), 4, 2), np.float64)
+
+    def corners(f):
+        o, u, v = (tuple(int(x) for x in F[f, a:a + 3]) for a in (0, 3, 6))
+        return [o, _vadd(o, u), _vadd(_vadd(o, u), v), _vadd(o, v)]
+
+    def normal(f):
+        return _vcross(tuple(int(x) for x in F[f, 3:6]), tuple(int(x) for x in F[f, 6:9]))
+
     for p, (i, j) in enumerate(zip(ii, jj)):
-        ni, nj = Ni[i], Ni[j]
-        if not np.cross(ni, nj).any():
+        ni, nj = normal(i), normal(j)
+        if _vcross(ni, nj) == (0, 0, 0):
             rel[p] = 1
-        elif int(ni @ nj) == 0:
+        elif _vdot(ni, nj) == 0:
             rel[p] = 2
-        corners_j = [O[j], O[j] + U[j], O[j] + U[j] + V[j], O[j] + V[j]]
-        # edge k of face i: (start, direction), opposite edge midpoint
-        c = [O[i], O[i] + U[i], O[i] + U[i] + V[i], O[i] + V[i]]
+        ci, cj = corners(i), corners(j)
         for k in range(4):
-            # doubled, so that midpoints are integers
-            mid2 = (c[k] + c[(k + 1) % 4]).astype(np.int64)
-            ref2 = (c[(k + 2) % 4] + c[(k + 3) % 4]).astype(np.int64) - mid2
+            e = _vsub(ci[(k + 1) % 4], ci[k])                    # the edge's direction
+            ee = _vdot(e, e)
+            mid2 = _vadd(ci[k], ci[(k + 1) % 4])                 # 2 B
+            ba2 = _vsub(_vadd(ci[(k + 2) % 4], ci[(k + 3) % 4]), mid2)
+            ref = _vsub(_vscale(ee, ba2), _vscale(_vdot(ba2, e), e))   # ee * 2 * BA, projected
             om = []
-            for Fc in corners_j:
-                d2 = 2 * Fc.astype(np.int64) - mid2
-                dot = int(ref2 @ d2)
-                if not np.cross(ref2, d2).any() and dot < 0:
-                    om.append(0.0)          # exactly 180 degrees: recorded as 0
+            for c in cj:
+                bf2 = _vsub(_vscale(2, c), mid2)
+                w = _vsub(_vscale(ee, bf2), _vscale(_vdot(bf2, e), e))  # ee * 2 * BF, projected
+                side = _vdot(w, ni)
+                along = _vdot(w, ref)
+                if w == (0, 0, 0) or side < 0 or (side == 0 and along < 0):
+                    om.append(0.0)                               # no direction, or >= 180
                     continue
-                cosv = dot / (math.sqrt(int(ref2 @ ref2)) * math.sqrt(int(d2 @ d2)))
-                w = math.degrees(math.acos(min(1.0, max(-1.0, cosv))))
-                om.append(w)
+                cosv = along / (math.sqrt(_vdot(ref, ref)) * math.sqrt(_vdot(w, w)))
+                om.append(math.degrees(math.acos(min(1.0, max(-1.0, cosv)))))
             rng[p, k] = (min(om), max(om))
     return pairs, rel, rng
+
+
+def _vadd(a, b):
+    return (a[0] + b[0], a[1] + b[1], a[2] + b[2])
+
+
+def _vsub(a, b):
+    return (a[0] - b[0], a[1] - b[1], a[2] - b[2])
+
+
+def _vscale(k, a):
+    return (k * a[0], k * a[1], k * a[2])
+
+
+def _vdot(a, b):
+    return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]
+
+
+def _vcross(a, b):
+    return (a[1] * b[2] - a[2] * b[1], a[2] * b[0] - a[0] * b[2], a[0] * b[1] - a[1] * b[0])

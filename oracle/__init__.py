@@ -552,7 +552,12 @@ def interface_relations(facets, M, n_facets=None):
                 if w == (0, 0, 0) or side < 0 or (side == 0 and along < 0):
                     om.append(0.0)                               # no direction, or >= 180
                     continue
-                cosv = along / (math.sqrt(_vdot(ref, ref)) * math.sqrt(_vdot(w, w)))
+                # w and ref are ee times the projected vectors, so each of
+                # these products is ee times an integer; the cosine is taken
+                # from those integers (one rounding each on conversion)
+                ww, rr = _vdot(w, w), _vdot(ref, ref)
+                assert along % ee == 0 and ww % ee == 0 and rr % ee == 0
+                cosv = (along // ee) / (math.sqrt(ww // ee) * math.sqrt(rr // ee))
                 om.append(math.degrees(math.acos(min(1.0, max(-1.0, cosv)))))
             rng[p, k] = (min(om), max(om))
     return pairs, rel, rng

@@ -293,6 +293,7 @@ def degenerate(seed=3, n_snap=10000):
     rx = np.stack([10000 + (10 * t) // 3, np.full(n_snap, 50000),
                    np.full(n_snap, 150)], 1)
     kinds = []
+    grazing = []    # snapshots t* whose Tx-Rx line a kind-3 building's edge sits on
     k = 0
     guard = 0
     while len(pl.boxes) < 200:
@@ -336,11 +337,13 @@ def degenerate(seed=3, n_snap=10000):
         if ok:
             pl.add(box)
             kinds.append(kind)
+            if kind == 3:
+                grazing.append(ts)
             k += 1
     tx = np.tile(np.array([tx_pt]), (n_snap, 1))
     return Scene("degenerate", facets_from_boxes(side, pl.boxes), tx.astype(np.int32),
                  rx.astype(np.int32), 5, 3, pl.boxes, side,
-                 {"tx": tx_pt, "degenerate_kinds": kinds})
+                 {"tx": tx_pt, "degenerate_kinds": kinds, "grazing_snapshots": grazing})
 
 
 def batch_scene(k, n_buildings=None, n_snap=None):

@@ -63,6 +63,33 @@ def test_grid_equals_brute_force_on_degenerate_samples():
     _brute_vs_grid(sc, rows=rows, snaps=snaps)
 
 
+@pytest.mark.parametrize("name,make", [("district", sg.district), ("degenerate", sg.degenerate)])
+def test_grid_equals_stored_brute_force_matrix(name, make):
+    """Full matrix, grid mode against the brute-force bits written by
+    tests/golden/make_oracle_matrices.py."""
+    path = os.path.join(GOLDEN, f"oracle_matrix_{name}.npz")
+    z = np.load(path)
+    sc = make()
+    from tests.golden.make_oracle_matrices import digest
+    assert str(z["digest"]) == digest(sc.facets, sc.samples_per_side), "stale golden file"
+    M = oracle.matrix(sc.facets, sc.samples_per_side, mode="grid")
+    assert (M == z["matrix"]).all()
+
+
+def test_grid_equals_stored_brute_force_table_near_grazing_snapshots():
+    """The degenerate district's table rows within 16 snapshots of each t*
+    (a building edge on the Tx-Rx line in plan), grid mode against the stored
+    brute-force rows."""
+    from tests.golden.make_oracle_matrices import digest, grazing_window
+    z = np.load(os.path.join(GOLDEN, "oracle_table_degenerate.npz"))
+    sc = sg.degenerate()
+    snaps = grazing_window(sc)
+    assert (z["snaps"] == snaps).all()
+    assert str(z["digest"]) == digest(sc.facets, sc.samples_per_side, sc.tx[snaps], sc.rx[snaps])
+    tab, los = oracle.table(sc.facets, sc.samples_per_side, sc.tx, sc.rx, snaps=snaps, mode="grid")
+    assert (tab == z["table"]).all() and (los == z["los"]).all()
+
+
 def _triangles(F, s):
     """The two triangles of every facet, scaled by 2s: [2N][3][3] int64."""
     F = F.astype(np.int64)

@@ -395,17 +395,26 @@ const char *ivm_strerror(int code);
  * device array of the library (about 5 MB, held on every GPU that loads the
  * library until the process exits).
  *   facets  device pointer, n_facets records (1..IVM_NOALLOC_MAX_FACETS);
- *   params  samples_per_side 1..IVM_NOALLOC_MAX_SAMPLES_PER_SIDE, mode and
- *           the PERSISTENT / OCCLUDER_CACHE flags as for ivm_build_matrix;
+ *   params  samples_per_side 1..IVM_NOALLOC_MAX_SAMPLES_PER_SIDE; mode
+ *           IVM_MODE_EXACT or IVM_MODE_FILTERED (there is no ranker without a
+ *           context, so IVM_MODE_LEARNED is refused); the PERSISTENT and
+ *           OCCLUDER_CACHE flags, warps_per_block and tile as for
+ *           ivm_build_matrix (0 = default); IVM_FLAG_GRAPH and
+ *           IVM_FLAG_DEDUP_SOURCES have no effect here;
  *   matrix  device pointer, [n_facets][W] words, written as ivm_build_matrix;
  *   cuda_stream  cudaStream_t of the current device (NULL: legacy stream).
- * Runs on the current device.  The first call on a device looks up the
- * array's device address (cudaGetSymbolAddress); make that first call
- * before any stream capture.  Calls share the array: each call clears what
- * must start at zero, and calls that overlap on the GPU race on it.  It
- * synchronises the stream before returning.  Errors: IVM_ERR_ARG (null
- * pointer, or n_facets / samples_per_side above the limits), IVM_ERR_RANGE,
- * IVM_ERR_TIMEOUT, IVM_ERR_INTERNAL, IVM_ERR_CUDA. */
+ * facets and matrix must be memory of the current device (or managed
+ * memory); anything else is refused with IVM_ERR_ARG before any work is
+ * enqueued.  Runs on the current device.  The first call on a device looks
+ * up the array's device address (cudaGetSymbolAddress) and keeps it for the
+ * life of the process; make that first call before any stream capture, and
+ * do not call the entry point on a device after cudaDeviceReset of that
+ * device (the kept address is stale then).  Calls share the array: each
+ * call clears what must start at zero, and calls that overlap on the GPU
+ * race on it.  It synchronises the stream before returning.  Errors:
+ * IVM_ERR_ARG (null or non-device pointer, learned mode, n_facets /
+ * samples_per_side above the limits), IVM_ERR_RANGE, IVM_ERR_TIMEOUT,
+ * IVM_ERR_INTERNAL, IVM_ERR_CUDA. */
 #define IVM_NOALLOC_MAX_FACETS 1024
 #define IVM_NOALLOC_MAX_SAMPLES_PER_SIDE 5
 int ivm_build_matrix_noalloc(const ivm_facet *facets, int32_t n_facets, const ivm_params *params,

@@ -13,7 +13,9 @@
 // exits.  In host code the array's name is only a host-side stand-in, so its
 // device address is looked up with cudaGetSymbolAddress, once per device, on
 // the first call made with that device current (that first call should
-// therefore come before any stream capture).  All calls share the array and
+// therefore come before any stream capture).  The address is kept for the
+// life of the process: after cudaDeviceReset on that device it is stale, and
+// the entry point must not be called again on that device.  All calls share the array and
 // it keeps the last call's contents: everything that must start at zero is
 // cleared by each call, and two calls that overlap on the GPU (on different
 // streams, or from different host threads) race on it.
@@ -86,6 +88,21 @@ static int scratch_base(int dev, unsigned char **out)
         }                                       \
     } while (0)
 
+// True when p is device (or managed) memory that the current device dev can
+// use.  A host pointer or another GPU's memory would make the kernels read an
+// address they cannot reach, so such arguments are refused before anything is
+// enqueued.
+static bool on_device(const void *p, int dev)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    if (a.type == cudaMemoryTypeManaged) return true;
+    return a.type == cudaMemoryTypeDevice && a.device == dev;
+}
+
 static int noalloc_error(unsigned char *base, cudaStream_t st)
 {
     int h = 0;
@@ -102,9 +119,14 @@ extern "C" int ivm_build_matrix_noalloc(const ivm_facet *facets, int32_t n_facet
     if (n_facets < 1 || n_facets > kMaxN) return IVM_ERR_ARG;
     const int s = params->samples_per_side;
     if (s < 1 || s > kMaxS) return IVM_ERR_ARG;
-    if (params->mode < IVM_MODE_EXACT || params->mode > IVM_MODE_LEARNED) return IVM_ERR_ARG;
+    // no context, hence no ranker: the learned form is refused rather than
+    // silently run as the filtered one
+    if (params->mode != IVM_MODE_EXACT && params->mode != IVM_MODE_FILTERED) return IVM_ERR_ARG;
+    if (params->tile < 0 || params->warps_per_block < 0 || params->warps_per_block > 4)
+        return IVM_ERR_ARG;
     int dev = 0;
     NA_CK(cudaGetDevice(&dev));
+    if (!on_device(facets, dev) || !on_device(matrix, dev)) return IVM_ERR_ARG;
     unsigned char *base = nullptr;
     int r = scratch_base(dev, &base);
     if (r) return r;
@@ -170,8 +192,8 @@ extern "C" int ivm_build_matrix_noalloc(const ivm_facet *facets, int32_t n_facet
     LaunchCfg cfg;
     cfg.mode = params->mode == IVM_MODE_EXACT ? IVM_MODE_EXACT : IVM_MODE_FILTERED;
     cfg.persistent = (params->flags & IVM_FLAG_PERSISTENT) != 0;
-    cfg.warps_per_block = 4;
-    cfg.tile = cfg.persistent ? 4 : 1;
+    cfg.warps_per_block = params->warps_per_block > 0 ? params->warps_per_block : 4;
+    cfg.tile = params->tile > 0 ? params->tile : (cfg.persistent ? 4 : 1);
     cfg.n_sm = n_sm;
     cfg.cache = (params->flags & IVM_FLAG_OCCLUDER_CACHE) != 0;
     cfg.dedup = 0;

@@ -38,8 +38,12 @@ def _noalloc(stream, F, s, mode, flags):
     (ivm.IVM_MODE_FILTERED, ivm.IVM_FLAG_PERSISTENT | ivm.IVM_FLAG_OCCLUDER_CACHE)])
 def test_noalloc_matches_regular_entry_point_twice(env, mode, flags):
     ctx, stream = env
+    one = sg.tiny().facets[:1]                                   # no pair at all
+    full = sg.batch_scene(3, n_buildings=260, n_snap=1).facets[:ivm.NOALLOC_MAX_FACETS]
+    assert full.shape[0] == ivm.NOALLOC_MAX_FACETS               # the size limit, at s = 5
     scenes = [(sg.district().facets, 5), (sg.tiny().facets, 3),
-              (sg.random_small_city(601, n_buildings=6, s=2).facets, 2)]
+              (sg.random_small_city(601, n_buildings=6, s=2).facets, 2), (one, 3),
+              (full, ivm.NOALLOC_MAX_SAMPLES_PER_SIDE)]
     want = []
     for F, s in scenes:
         M, _ = ivm.ivm_build_matrix(ctx, F, s, mode=mode, flags=flags)
@@ -65,3 +69,24 @@ def test_noalloc_rejects_sizes_beyond_its_limits(env):
     F = sg.tiny().facets
     code, got = _noalloc(stream, F, 3, ivm.IVM_MODE_EXACT, 0)
     assert code == ivm.IVM_OK and got.shape == (41, 2)
+
+
+def test_noalloc_refuses_host_memory_and_the_learned_form(env):
+    """Host memory cannot be read by the kernels: the call must refuse it
+    before anything is enqueued.  The learned form needs a context's ranker."""
+    import torch
+    _, stream = env
+    F = np.ascontiguousarray(sg.tiny().facets)
+    W = ivm.words(F.shape[0])
+    out_h = np.zeros((F.shape[0], W), dtype=np.int32)
+    out_d = torch.zeros((F.shape[0], W), dtype=torch.int32, device="cuda")
+    fd = torch.from_numpy(F).cuda()
+    assert ivm.ivm_build_matrix_noalloc(F, 3, out_d, stream) == ivm.IVM_ERR_ARG
+    assert ivm.ivm_build_matrix_noalloc(fd, 3, out_h, stream) == ivm.IVM_ERR_ARG
+    assert ivm.ivm_build_matrix_noalloc(fd, 3, out_d, stream,
+                                        mode=ivm.IVM_MODE_LEARNED) == ivm.IVM_ERR_ARG
+    torch.cuda.synchronize()
+    assert int(out_d.abs().sum().item()) == 0                    # nothing was written
+    code, got = _noalloc(stream, F, 3, ivm.IVM_MODE_FILTERED, 0)
+    want, _ = ivm.ivm_build_matrix(env[0], F, 3, mode=ivm.IVM_MODE_FILTERED)
+    assert code == ivm.IVM_OK and (got == want.cpu().numpy()).all()

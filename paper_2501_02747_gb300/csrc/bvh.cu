@@ -208,8 +208,15 @@ cudaError_t launch_bvh(const DevScenes &g, cudaStream_t st)
     dim3 grid((g.max_n + 255) / 256, g.n_scenes);
     k_rank_sort<<<grid, 256, 0, st>>>(g, g.sorted);
     k_karras<<<grid, 256, 0, st>>>(g, g.sorted);
-    if (g.total_nodes > 0)
-        cudaMemsetAsync(g.visits, 0, sizeof(int) * (size_t)g.total_nodes, st);
+    if (g.total_nodes > 0) {
+        // the refit's arrival counters must start at zero: a failed clear
+        // would leave the previous call's counts, so it ends the build here
+        cudaError_t e = cudaMemsetAsync(g.visits, 0, sizeof(int) * (size_t)g.total_nodes, st);
+        if (e != cudaSuccess) {
+            note_launches(5);
+            return e;
+        }
+    }
     k_refit<<<nb, 256, 0, st>>>(g);
     note_launches(7);
     return cudaGetLastError();

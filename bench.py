@@ -1,24 +1,35 @@
 #!/usr/bin/env python
 """Benchmark of the inter-visibility hot path on GB300.
 
-One step = one pass of the whole path over the district workload (1 km
-square, 200 box buildings, 1,001 facets, 5 x 5 samples per facet, 10,000
-Rx snapshots at 120 km/h every 1 ms, rooftop Tx, reflection order 3):
-ivm_build_matrix (ingest, BVH, facing screen, sample-pair occlusion),
-ivm_build_table (Tx and Rx rows and the direct path per snapshot) and
-ivm_expand_image_tree (orders 0..3, counts and fingerprints).
+Headline workload: the 25k-facet city (4 km square, 5,000 box buildings,
+25,001 facets, 3 x 3 samples per facet, 100,000 Rx snapshots at 350 km/h
+every 1 ms along a serpentine, rooftop Tx, reflection order 3).  One step =
+one pass of the whole path over it: ivm_build_matrix (ingest, BVH, facing
+screen, sample-pair occlusion), ivm_build_table (Tx and Rx rows and the
+direct path per snapshot) and ivm_expand_image_tree (orders 0..3, counts
+and fingerprints).
 
 Metric: visibility pair-tests per second: the N^2 ordered facet pairs the
 matrix decides plus the 2 N S Tx/Rx-facet pairs the table decides, per step,
 divided by the step time.  Snapshot tables per second (S / step time) is
-reported beside it.
+reported beside it.  Three forms run on the same step: fast (FP32 filter with
+exact fallback, persistent queues, occluder caches, row deduplication, graph
+replay, autotuned shape), plain (exact integer tests, one warp per item, no
+caches) and learned (fast + the trained cluster ranker); their outputs are
+compared bit for bit.
 
 `value` is device time (CUDA events on the library's stream) with inputs
 resident in HBM; L2 is flushed between steps by writing a 512 MB buffer
 outside the timed events.  `e2e` is the same metric through the same C-ABI
 calls with pinned host buffers (every copy inside the timed region).
-`--impl reference` times the CPU oracle (the brute-force definition) on the
-host cores instead.
+Beside the headline: the roofline of the dominant kernel (FP32 work per
+Sec. 8(d)'s count of the method's tests), the precision form on the
+degenerate district (undecided fraction, mismatches against stored
+brute-force oracle bits), the 64-scene batch (one batched, persistent,
+graph-replayed call per phase against the plain form), the district step and
+the district's further outputs (visibility ranges, ray validation, edges,
+interface relations), and the CPU oracle on the host cores.
+`--impl reference` times the CPU oracle on the city instead.
 """
 from __future__ import annotations
 
@@ -36,11 +47,18 @@ sys.path.insert(0, ROOT)
 
 METRIC = "visibility pair-tests/s and Tx/Rx snapshot tables/s, bit-exact, vs plain GPU form"
 UNIT = "pair-tests/s"
-WORKLOAD = ("district: 1 km x 1 km, 200 box buildings (8-40 m footprint, 6-60 m high), "
+CITY = ("city: 4 km x 4 km, 5,000 box buildings (8-40 m footprint, 6-60 m high), 25,001 facets, "
+        "3x3 samples per facet, 100,000 Rx snapshots at 350 km/h every 1 ms along a serpentine, "
+        "rooftop Tx, reflection order <= 3, seed 5")
+DISTRICT = ("district: 1 km x 1 km, 200 box buildings (8-40 m footprint, 6-60 m high), "
             "1,001 facets, 5x5 samples per facet, 10,000 Rx snapshots at 120 km/h every 1 ms, "
             "rooftop Tx, reflection order <= 3, seed 2")
-FP32_OPS_PER_NODE_TEST = 30      # seg_box: 3 axes x 8 + 6 for the widening
-FP32_OPS_PER_FILTERED_LEAF = 104  # 4 edges x 26 (value, permanent, bound, compare)
+# FP32 work per test, as the method's algorithmic count: a segment-box slab
+# test about 12 FLOP, a segment-facet test about 50 FLOP; a fused multiply-add
+# counts as 2 FLOP in the peak.
+FLOP_PER_BOX_TEST = 12
+FLOP_PER_FACET_TEST = 50
+GOLDEN = os.path.join(ROOT, "tests", "golden")
 
 
 def parse():
@@ -51,10 +69,13 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
-    # profiling case: one phase of one form on the first N snapshots (no JSON contract line)
+    # profiling case: one phase of one form on a slice of a workload (no JSON contract line)
     p.add_argument("--profile", choices=["matrix", "table", "tree", "step"], default=None)
+    p.add_argument("--workload", choices=["city", "district"], default="city")
     p.add_argument("--form", choices=["fast", "plain", "learned"], default="fast")
     p.add_argument("--snapshots", type=int, default=None)
+    p.add_argument("--rows", type=int, default=None,
+                   help="profiling: decide only the pairs of the first ROWS matrix rows")
     return p.parse_args()
 
 
@@ -152,7 +173,7 @@ class Clocks:
 
 # ------------------------------------------------------------------ CPU oracle
 
-def oracle_sample(sc, n_rows, n_snaps, seed, threads):
+def oracle_sample(sc, n_rows, n_snaps, seed, threads, mode):
     """Oracle on a bounded sample of the workload; returns (pair tests, s)."""
     import numpy as np
 
@@ -161,11 +182,18 @@ def oracle_sample(sc, n_rows, n_snaps, seed, threads):
     rows = rng.choice(sc.n_facets, n_rows, replace=False)
     snaps = rng.choice(sc.n_snap, n_snaps, replace=False)
     t0 = time.perf_counter()
-    oracle.matrix(sc.facets, sc.samples_per_side, rows=rows, threads=threads)
-    oracle.table(sc.facets, sc.samples_per_side, sc.tx, sc.rx, snaps=snaps, threads=threads)
+    oracle.matrix(sc.facets, sc.samples_per_side, rows=rows, threads=threads, mode=mode)
+    oracle.table(sc.facets, sc.samples_per_side, sc.tx, sc.rx, snaps=snaps, threads=threads,
+                 mode=mode)
     dt = time.perf_counter() - t0
     units = n_rows * sc.n_facets + 2 * n_snaps * sc.n_facets
     return units, dt
+
+
+ORACLE_GRID = ("oracle/ivm_oracle.c in grid mode: the brute-force definition's exact int128 "
+               "triangle test, each segment tested against the triangles an exact xy grid "
+               "cannot rule out (bit-identical to brute force, which is infeasible at this "
+               "size: about 3e16 triangle tests for the matrix)")
 
 
 def run_reference(args, ws, rank):
@@ -174,26 +202,25 @@ def run_reference(args, ws, rank):
     import oracle
     from paper_2501_02747_gb300 import scenegen as sg
     oracle.build()
-    sc = sg.district()
+    sc = sg.city()
     threads = os.cpu_count() or 1
     for k in range(args.warmup):
-        oracle_sample(sc, 1, 2, 100 + k, threads)
+        oracle_sample(sc, 1, 2, 100 + k, threads, "grid")
     units = 0
     secs = 0.0
     for k in range(args.steps):
-        u, dt = oracle_sample(sc, 4, 16, 200 + k, threads)
+        u, dt = oracle_sample(sc, 16, 32, 200 + k, threads, "grid")
         units += u
         secs += dt
     value = units / secs
-    sample = (f"per step: 4 seeded matrix rows (4 x 1,001 ordered pairs) and 16 seeded "
-              f"snapshots (16 x 2 x 1,001 Tx/Rx-facet pairs) of the district workload")
+    sample = ("per step: 16 seeded matrix rows (16 x 25,001 ordered pairs) and 32 seeded "
+              "snapshots (32 x 2 x 25,001 Tx/Rx-facet pairs) of the city workload")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
         "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "int128",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "oracle": "brute force, every segment against every "
-                   "triangle, exact int128 (oracle/ivm_oracle.c)"},
+        "config": {"workload": CITY, "oracle": ORACLE_GRID},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -221,8 +248,424 @@ def traffic_from_profiles(kernel):
         return None
 
 
-def run_ours(args, ws, rank, local):
+def fp32_flop(st):
+    """The method's FP32 work in one call's traversal, from its own counters:
+    box tests x 12 plus facet tests the FP32 filter decided x 50."""
+    return (st["node_tests"] * FLOP_PER_BOX_TEST +
+            max(st["leaf_tests"] - st["exact_tests"], 0) * FLOP_PER_FACET_TEST)
+
+
+def popcount(a):
     import numpy as np
+    return int(np.unpackbits(np.ascontiguousarray(a).view(np.uint8)).sum())
+
+
+class Path:
+    """Device buffers and the three calls of one step over one scene; with
+    ws > 1 this rank's share (its matrix rows, the all-reduce of the parts,
+    then the table and tree of its snapshot range)."""
+
+    def __init__(self, ivm, shard, ctx, sc, dev, ws, rank, tuned, stream):
+        import torch
+        self.ivm, self.shard, self.ctx, self.sc, self.ws = ivm, shard, ctx, sc, ws
+        self.stream = stream
+        N, S = sc.n_facets, sc.n_snap
+        self.N, self.S, self.K, self.s = N, S, sc.max_order, sc.samples_per_side
+        self.W = ivm.words(N)
+        self.units = N * N + 2 * N * S   # the whole job's units (split across ranks)
+        self.rows = shard.row_ranges(N, ws)[rank]
+        self.snap = shard.snapshot_ranges(S, ws)[rank]
+        self.fac = torch.from_numpy(sc.facets).to(dev)
+        self.tx = torch.from_numpy(sc.tx).to(dev)
+        self.rx = torch.from_numpy(sc.rx).to(dev)
+        self.M = torch.empty((N, self.W), dtype=torch.int32, device=dev)
+        self.T = torch.empty((S, 2, self.W), dtype=torch.int32, device=dev)
+        self.L = torch.empty((S,), dtype=torch.uint8, device=dev)
+        self.summ = torch.empty((S, self.K + 1, 3), dtype=torch.int64, device=dev)
+        fast = (ivm.IVM_FLAG_PERSISTENT | ivm.IVM_FLAG_OCCLUDER_CACHE |
+                ivm.IVM_FLAG_DEDUP_SOURCES | ivm.IVM_FLAG_GRAPH)
+        self.forms = {"plain": dict(mode=ivm.IVM_MODE_EXACT, flags=0),
+                      "fast": dict(mode=ivm.IVM_MODE_FILTERED, flags=fast),
+                      "learned": dict(mode=ivm.IVM_MODE_LEARNED, flags=fast)}
+        self.tuned = tuned
+        sm = {"tile": tuned["tile"], "warps_per_block": tuned["warps_per_block"]}
+        stt = {"tile": tuned["table_tile"], "warps_per_block": tuned["warps_per_block"]}
+        self.shape = {"plain": ({}, {}), "fast": (sm, stt), "learned": (sm, stt)}
+
+    def outputs(self):
+        return (self.M, self.T, self.L, self.summ)
+
+    def step(self, form, bufs=None, marks=None):
+        """The three calls; `marks` (4 CUDA events) bracket them on the stream."""
+        ivm = self.ivm
+        fac, tx, rx, M, T, L, summ = bufs or (self.fac, self.tx, self.rx) + self.outputs()
+        kw = self.forms[form]
+        kw_m, kw_t = self.shape[form]
+        if marks:
+            marks[0].record(self.stream)
+        if self.ws == 1:
+            _, stm = ivm.ivm_build_matrix(self.ctx, fac, self.s, out=M, **kw, **kw_m)
+        else:
+            _, stm = ivm.ivm_build_matrix_rows(self.ctx, fac, self.s, self.rows, out=M, **kw,
+                                               **kw_m)
+            self.shard.exchange_matrix(M)
+        if marks:
+            marks[1].record(self.stream)
+        a, b = self.snap
+        _, stt = ivm.ivm_build_table(self.ctx, fac, self.s, tx[a:b], rx[a:b],
+                                     out=(T[a:b], L[a:b]), **kw, **kw_t)
+        if marks:
+            marks[2].record(self.stream)
+        ivm.ivm_expand_image_tree(self.ctx, M, T[a:b], L[a:b], self.N, self.K,
+                                  summary=summ[a:b])
+        if marks:
+            marks[3].record(self.stream)
+        return stm, stt
+
+
+def timed(path, form, steps, warmup, flush, ws, clocks=None):
+    """W untimed steps, then K steps timed with CUDA events on the library's
+    stream, L2 flushed between them (outside the events); the max over ranks."""
+    import torch
+    ivm = path.ivm
+    for _ in range(warmup):
+        path.step(form)
+    torch.cuda.synchronize()
+    barrier(ws)
+    torch.cuda.synchronize()
+    if clocks:
+        clocks.start()
+    launches0 = ivm.kernel_launches()
+    times = []
+    calls = {"matrix": 0.0, "table": 0.0, "tree": 0.0}
+    kern = {"matrix": 0.0, "table": 0.0}
+    flop = {"matrix": 0.0, "table": 0.0}
+    stats = None
+    torch.cuda.nvtx.range_push(f"timed_{form}")
+    for _ in range(steps):
+        flush.zero_()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        stm, stt = path.step(form, marks=ev)
+        torch.cuda.synchronize()
+        times.append(ev[0].elapsed_time(ev[3]))
+        for k, name in enumerate(("matrix", "table", "tree")):
+            calls[name] += ev[k].elapsed_time(ev[k + 1]) / steps
+        stats = {"matrix": stm.as_dict(), "table": stt.as_dict()}
+        for name in ("matrix", "table"):
+            kern[name] += stats[name]["ms_traverse"] / steps
+            flop[name] += fp32_flop(stats[name]) / steps
+    torch.cuda.nvtx.range_pop()
+    launches = ivm.kernel_launches() - launches0
+    clk = clocks.stop() if clocks else None
+    torch.cuda.synchronize()
+    barrier(ws)
+    ms = max_over_ranks(ws, sum(times)) / steps
+    return {"ms": ms, "steps": steps, "warmup": warmup, "calls": calls, "kern": kern,
+            "flop": flop, "stats": stats, "launches": launches, "clocks": clk}
+
+
+def same_outputs(path, forms):
+    """Runs one step per form and compares every output with the first's."""
+    import torch
+    ref = None
+    agree = True
+    for form in forms:
+        path.step(form)
+        torch.cuda.synchronize()
+        now = tuple(x.clone() for x in path.outputs())
+        if ref is None:
+            ref = now
+        else:
+            agree &= all(bool((a == b).all()) for a, b in zip(ref, now))
+        del now
+    return agree
+
+
+def roofline(t, ivm, ctx, n_sm, traffic_name):
+    """Roofline of the dominant traversal kernel of a timed form `t`."""
+    peaks = {}
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        peaks = json.load(open(p))
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    dom = "table" if t["kern"]["table"] >= t["kern"]["matrix"] else "matrix"
+    kname = {"table": "k_table", "matrix": "k_matrix"}[dom]
+    peak = n_sm * 128 * 2 * sm_max * 1e6 / 1e12
+    ms = t["kern"][dom]
+    achieved = t["flop"][dom] / (ms / 1e3) / 1e12 if ms > 0 else 0.0
+    st = t["stats"][dom]
+    ffma = 2 * ivm.ivm_fp32_peak(ctx) / 1e12
+    return {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak,
+            "unit": "TFLOP/s", "frac": achieved / peak if peak else None,
+            "traffic": traffic_from_profiles(f"{kname}_{traffic_name}"),
+            "peak_basis": f"nominal FP32: {n_sm} SMs x 128 lanes x 2 FLOP per FMA x "
+                          f"{sm_max:.0f} MHz (sm_max_mhz of MEASURED_PEAKS.json)",
+            "work_basis": f"{FLOP_PER_BOX_TEST} FLOP per segment-box test (node_tests) + "
+                          f"{FLOP_PER_FACET_TEST} FLOP per facet test decided in FP32 "
+                          "(leaf_tests - exact_tests), per launch",
+            "ms_per_launch": ms, "flop_per_launch": t["flop"][dom],
+            "node_tests": st["node_tests"], "leaf_tests": st["leaf_tests"],
+            "exact_tests": st["exact_tests"], "segments": st["segments"],
+            "peak_measured_ffma": ffma,
+            "frac_of_measured_ffma": achieved / ffma if ffma else None,
+            "kernel_ms_per_step": dict(t["kern"])}
+
+
+def profile_case(args, ivm, shard, sg, ctx, dev, stream):
+    """One phase of one form on a slice of a workload (launch shape as timed);
+    the calls after the warm-up run inside the NVTX range "profile_<phase>"
+    (ncu --nvtx --nvtx-include).  Prints the last call's counters."""
+    import torch
+    sc = sg.city() if args.workload == "city" else sg.district()
+    fd = torch.from_numpy(sc.facets).to(dev)
+    Sp = min(sc.n_snap, args.snapshots or sc.n_snap)
+    tx = torch.from_numpy(sc.tx[:Sp]).to(dev)
+    rx = torch.from_numpy(sc.rx[:Sp]).to(dev)
+    tuned = ivm.ivm_autotune(ctx, fd, sc.samples_per_side, tx, rx, mode=ivm.IVM_MODE_FILTERED,
+                             flags=ivm.IVM_FLAG_PERSISTENT | ivm.IVM_FLAG_OCCLUDER_CACHE |
+                             ivm.IVM_FLAG_DEDUP_SOURCES)
+    path = Path(ivm, shard, ctx, sc, dev, 1, 0, tuned, stream)
+    if args.form == "learned":
+        ivm.ivm_ranker_train(ctx, [sg.tiny().facets, sg.degenerate(n_snap=16).facets],
+                             sc.samples_per_side, epochs=12, lr=2e-3)
+    kw = path.forms[args.form]
+    kw_m, kw_t = path.shape[args.form]
+    s, N, K = path.s, path.N, path.K
+    rows = (0, min(N, args.rows)) if args.rows else None
+    st = None
+    for it in range(args.warmup + args.steps):
+        if it == args.warmup:
+            torch.cuda.synchronize()
+            torch.cuda.nvtx.range_push(f"profile_{args.profile}")
+        if args.profile in ("matrix", "step") or (args.profile == "tree" and it == 0):
+            if rows:
+                _, st = ivm.ivm_build_matrix_rows(ctx, fd, s, rows, out=path.M, **kw, **kw_m)
+            else:
+                _, st = ivm.ivm_build_matrix(ctx, fd, s, out=path.M, **kw, **kw_m)
+        if args.profile in ("table", "step") or (args.profile == "tree" and it == 0):
+            _, st = ivm.ivm_build_table(ctx, fd, s, tx, rx, out=(path.T[:Sp], path.L[:Sp]),
+                                        **kw, **kw_t)
+        if args.profile in ("tree", "step"):
+            ivm.ivm_expand_image_tree(ctx, path.M, path.T[:Sp], path.L[:Sp], N, K,
+                                      summary=path.summ[:Sp])
+    torch.cuda.synchronize()
+    if args.steps:
+        torch.cuda.nvtx.range_pop()
+    if args.profile in ("step", "tree"):
+        st = None
+    print(json.dumps({"profile": args.profile, "workload": args.workload, "form": args.form,
+                      "snapshots": Sp, "rows": rows, "tuned": tuned,
+                      "stats": st.as_dict() if st is not None else None}))
+
+
+def district_block(args, ivm, shard, sg, ctx, dev, stream, flush):
+    """The district step (fast and plain) and the district's further outputs,
+    each timed on its own: visibility ranges with their blockers and the
+    coherence time (Sec. III-C/D), image-method validation of image-tree
+    candidates (Sec. IV-B), edge rows and the nearest edge (Sec. III-B), edges
+    as matrix rows and columns, interface relations (Sec. II-B)."""
+    import numpy as np
+    import torch
+    sc = sg.district()
+    fd = torch.from_numpy(sc.facets).to(dev)
+    tuned = ivm.ivm_autotune(ctx, fd, sc.samples_per_side, torch.from_numpy(sc.tx).to(dev),
+                             torch.from_numpy(sc.rx).to(dev), mode=ivm.IVM_MODE_FILTERED,
+                             flags=ivm.IVM_FLAG_PERSISTENT | ivm.IVM_FLAG_OCCLUDER_CACHE |
+                             ivm.IVM_FLAG_DEDUP_SOURCES | ivm.IVM_FLAG_GRAPH)
+    p = Path(ivm, shard, ctx, sc, dev, 1, 0, tuned, stream)
+    tf = timed(p, "fast", args.steps, args.warmup, flush, 1)
+    tp = timed(p, "plain", args.steps, args.warmup, flush, 1)
+    agree = same_outputs(p, ["plain", "fast"])
+    N, s = p.N, p.s
+    p.step("fast")
+    torch.cuda.synchronize()
+    reps = max(3, min(args.steps, 10))
+
+    def med(fn):
+        ts = []
+        for it in range(1 + reps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            r = fn()
+            torch.cuda.synchronize()
+            if it:
+                ts.append(1e3 * (time.perf_counter() - t0))
+        return statistics.median(ts), r
+
+    ms, (recs, rsum) = med(lambda: ivm.ivm_visibility_ranges(ctx, p.fac, s, p.tx, p.rx, p.T))
+    tc = [rsum["snapshots"][x] / rsum["ranges"][x] if rsum["ranges"][x] else None
+          for x in range(2)]   # snapshots 1 ms apart
+    ranges_out = {
+        "what": "visibility ranges (maximal runs of each table bit), first blocker at both ends "
+                "of each, coherence time per Eq. (8)-(9); C-ABI call ivm_visibility_ranges on "
+                "the step's table, records copied to host",
+        "ms_per_call": ms, "ranges": int(len(recs)), "ranges_per_side": rsum["ranges"],
+        "coherence_time_ms": {"tx": tc[0], "rx": tc[1],
+                              "scenario": min(x for x in tc if x is not None) if any(tc) else None}}
+    a0, a1, rk = 0, 4, 2
+    _, n_cand = ivm.ivm_expand_image_tree(ctx, p.M, p.T[a0:a1], p.L[a0:a1], N, rk,
+                                          count_paths=True)
+    _, cand, n_cand, _ = ivm.ivm_expand_image_tree(ctx, p.M, p.T[a0:a1], p.L[a0:a1], N, rk,
+                                                   paths_capacity=max(n_cand, 1))
+    cand = cand[:n_cand]
+    flags = torch.zeros(max(n_cand, 1), dtype=torch.uint8, device=dev)
+    ms, _ = med(lambda: ivm.ivm_validate_paths(ctx, p.fac, s, p.tx[a0:a1], p.rx[a0:a1], cand,
+                                               rk, out=flags[:n_cand]))
+    rays_out = {"what": "image-method validation of image-tree candidates (orders 0-2) as "
+                        "specular rays, C-ABI call ivm_validate_paths, snapshots 0..3",
+                "candidates": int(n_cand), "valid_rays": int(flags[:n_cand].sum().item()),
+                "ms_per_call": ms}
+    E = torch.from_numpy(sg.edges_of(sc)).to(dev)
+    ms, (etab, _) = med(lambda: ivm.ivm_build_edge_table(ctx, p.fac, s, E, p.tx, p.rx,
+                                                         mode=ivm.IVM_MODE_FILTERED))
+    ne = int(E.shape[0])
+    edges_out = {"what": "edge rows (the 8 convex edges of every building, s samples each) and "
+                         "the nearest visible edge per source, C-ABI call ivm_build_edge_table",
+                 "edges": ne, "ms_per_call": ms,
+                 "edge_tests_per_s": 2 * ne * p.S / (ms / 1e3)}
+    EF = torch.from_numpy(sg.edge_faces_of(sc)).to(dev)
+    fe = torch.zeros((N, (ne + 31) // 32), dtype=torch.int32, device=dev)
+    ee = torch.zeros((ne, (ne + 31) // 32), dtype=torch.int32, device=dev)
+    ms, _ = med(lambda: ivm.ivm_build_edge_matrix(ctx, p.fac, s, E, EF, out=(fe, ee)))
+    edge_matrix_out = {"what": "edges as matrix rows and columns (facet-edge and edge-edge "
+                               "bits), C-ABI call ivm_build_edge_matrix",
+                       "facet_edge_pairs": N * ne, "edge_edge_pairs": ne * (ne - 1) // 2,
+                       "ms_per_call": ms,
+                       "facet_edge_bits": popcount(fe.cpu().numpy()),
+                       "edge_edge_bits": popcount(ee.cpu().numpy())}
+    ms, (rp, rr, _) = med(lambda: ivm.ivm_interface_relations(ctx, p.fac, s, p.M))
+    relations_out = {"what": "PAR/PER relation and angular bouncing ranges of every visible "
+                             "ordered pair, C-ABI call ivm_interface_relations",
+                     "pairs": int(len(rp)), "par": int((rr == 1).sum()),
+                     "per": int((rr == 2).sum()), "ms_per_call": ms}
+    return {"workload": DISTRICT, "autotuned_shape": tuned,
+            "fast": {"ms_per_step": tf["ms"], "value": p.units / (tf["ms"] / 1e3),
+                     "ms_per_call": tf["calls"]},
+            "plain": {"ms_per_step": tp["ms"], "value": p.units / (tp["ms"] / 1e3),
+                      "ms_per_call": tp["calls"]},
+            "speedup_vs_plain": tp["ms"] / tf["ms"], "forms_bit_identical": agree,
+            "steps": args.steps, "warmup": args.warmup,
+            "visibility_ranges": ranges_out, "ray_validation": rays_out, "edges": edges_out,
+            "edge_matrix": edge_matrix_out, "interface_relations": relations_out}
+
+
+def precision_block(ivm, sg, ctx, dev):
+    """The precision form on the degenerate district: the fraction of FP32
+    facet tests the filter could not decide (settled by exact integers), and
+    mismatches against stored brute-force oracle bits: the full matrix and
+    the table rows within 16 snapshots of each near-grazing snapshot."""
+    import numpy as np
+    import torch
+    from tests.golden.make_oracle_matrices import digest, grazing_window
+    sc = sg.degenerate()
+    s = sc.samples_per_side
+    fd = torch.from_numpy(sc.facets).to(dev)
+    fast = (ivm.IVM_FLAG_PERSISTENT | ivm.IVM_FLAG_OCCLUDER_CACHE | ivm.IVM_FLAG_DEDUP_SOURCES |
+            ivm.IVM_FLAG_GRAPH)
+    M, stm = ivm.ivm_build_matrix(ctx, fd, s, mode=ivm.IVM_MODE_FILTERED, flags=fast)
+    (T, L), stt = ivm.ivm_build_table(ctx, fd, s, torch.from_numpy(sc.tx).to(dev),
+                                      torch.from_numpy(sc.rx).to(dev),
+                                      mode=ivm.IVM_MODE_FILTERED, flags=fast)
+    torch.cuda.synchronize()
+    out = {"workload": "degenerate district: the district family with 10 of 200 buildings "
+                       "placed degenerately (shared wall spans, aligned facades, equal "
+                       "heights, vertical edges on Tx-Rx lines at snapshots "
+                       f"{sc.meta['grazing_snapshots']}), 5x5 samples, 10,000 snapshots",
+           "form": "FP32 filter with exact int64/int128 fallback (+ persistent, caches, graph)"}
+    for name, st in (("matrix", stm.as_dict()), ("table", stt.as_dict())):
+        out[name] = {"facet_tests": st["leaf_tests"], "undecided": st["undecided"],
+                     "undecided_fraction": st["undecided"] / st["leaf_tests"]
+                     if st["leaf_tests"] else 0.0,
+                     "ms_per_call": st["ms_total"]}
+    zm = np.load(os.path.join(GOLDEN, "oracle_matrix_degenerate.npz"))
+    zt = np.load(os.path.join(GOLDEN, "oracle_table_degenerate.npz"))
+    snaps = grazing_window(sc)
+    fresh = (str(zm["digest"]) == digest(sc.facets, s) and
+             str(zt["digest"]) == digest(sc.facets, s, sc.tx[snaps], sc.rx[snaps]) and
+             (zt["snaps"] == snaps).all())
+    Mg = M.cpu().numpy().view(np.uint32)
+    Tg = T.cpu().numpy().view(np.uint32)[snaps]
+    Lg = L.cpu().numpy()[snaps]
+    out["mismatches_vs_oracle"] = {
+        "matrix_bits": popcount(Mg ^ zm["matrix"]) if fresh else None,
+        "table_bits": popcount(Tg ^ zt["table"]) if fresh else None,
+        "los": int((Lg != zt["los"]).sum()) if fresh else None,
+        "checked": f"all {sc.n_facets}^2 matrix bits and the {len(snaps)} table rows and "
+                   "direct paths within 16 snapshots of each near-grazing snapshot",
+        "oracle": "brute force (every sample segment against every triangle, exact int128), "
+                  "stored by tests/golden/make_oracle_matrices.py",
+        "oracle_current": bool(fresh)}
+    return out
+
+
+def batch_block(args, ivm, sg, ctx, dev, stream, flush):
+    """The 64-scene batch: each phase as one batched call (persistent queues
+    over all scenes, graph replay, autotuned shape) against the plain form."""
+    import torch
+    scenes = sg.batch()
+    s = 3
+    fd = [torch.from_numpy(x.facets).to(dev) for x in scenes]
+    tx = [torch.from_numpy(x.tx).to(dev) for x in scenes]
+    rx = [torch.from_numpy(x.rx).to(dev) for x in scenes]
+    fast = (ivm.IVM_FLAG_PERSISTENT | ivm.IVM_FLAG_OCCLUDER_CACHE | ivm.IVM_FLAG_DEDUP_SOURCES |
+            ivm.IVM_FLAG_GRAPH)
+    t0 = time.perf_counter()
+    tuned = ivm.ivm_autotune(ctx, fd, s, tx, rx, mode=ivm.IVM_MODE_FILTERED, flags=fast)
+    tune_s = time.perf_counter() - t0
+
+    def bufs():
+        Ms = [torch.empty((x.n_facets, ivm.words(x.n_facets)), dtype=torch.int32, device=dev)
+              for x in scenes]
+        Ts = [(torch.empty((x.n_snap, 2, ivm.words(x.n_facets)), dtype=torch.int32, device=dev),
+               torch.empty((x.n_snap,), dtype=torch.uint8, device=dev)) for x in scenes]
+        return Ms, Ts
+
+    forms = {"fast": (dict(mode=ivm.IVM_MODE_FILTERED, flags=fast,
+                           tile=tuned["tile"], warps_per_block=tuned["warps_per_block"]),
+                      dict(mode=ivm.IVM_MODE_FILTERED, flags=fast,
+                           tile=tuned["table_tile"], warps_per_block=tuned["warps_per_block"])),
+             "plain": (dict(mode=ivm.IVM_MODE_EXACT), dict(mode=ivm.IVM_MODE_EXACT))}
+    res, outs = {}, {}
+    for form, steps, warm in (("fast", min(args.steps, 3), 1), ("plain", 1, 0)):
+        Ms, Ts = bufs()
+        kw_m, kw_t = forms[form]
+        ms_m, ms_t = [], []
+        for it in range(warm + steps):
+            flush.zero_()
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            ev[0].record(stream)
+            ivm.ivm_build_matrix(ctx, fd, s, out=Ms, **kw_m)
+            ev[1].record(stream)
+            ivm.ivm_build_table(ctx, fd, s, tx, rx, out=Ts, **kw_t)
+            ev[2].record(stream)
+            torch.cuda.synchronize()
+            if it >= warm:
+                ms_m.append(ev[0].elapsed_time(ev[1]))
+                ms_t.append(ev[1].elapsed_time(ev[2]))
+        res[form] = {"steps": steps, "warmup": warm,
+                     "matrix_ms_per_call": statistics.mean(ms_m),
+                     "table_ms_per_call": statistics.mean(ms_t)}
+        outs[form] = (Ms, Ts)
+    agree = all(bool((a == b).all()) for a, b in zip(outs["fast"][0], outs["plain"][0]))
+    agree &= all(bool((a[0] == b[0]).all()) and bool((a[1] == b[1]).all())
+                 for a, b in zip(outs["fast"][1], outs["plain"][1]))
+    units = sum(x.n_facets ** 2 + 2 * x.n_facets * x.n_snap for x in scenes)
+    for form in res:
+        ms = res[form]["matrix_ms_per_call"] + res[form]["table_ms_per_call"]
+        res[form]["ms_per_step"] = ms
+        res[form]["value"] = units / (ms / 1e3)
+    return {"workload": "64 seeded scenes of 50-2,000 box buildings (251-9,786 facets, sum of "
+                        "N^2 = 9.06e8), 791,715 snapshots in all, 3x3 samples",
+            "form": "one batched call per phase over all 64 scenes: FP32 filter + exact "
+                    "fallback, persistent work queues, caches, row deduplication, CUDA-graph "
+                    "replay, launch shape from the autotuner",
+            "autotuned_shape": tuned, "autotune_s": tune_s, "pair_tests_per_step": units,
+            "fast": res["fast"], "plain": res["plain"],
+            "speedup_vs_plain": res["plain"]["ms_per_step"] / res["fast"]["ms_per_step"],
+            "forms_bit_identical": agree}
+
+
+def run_ours(args, ws, rank, local):
     import torch
 
     from paper_2501_02747_gb300 import build, ivm, shard
@@ -231,361 +674,110 @@ def run_ours(args, ws, rank, local):
     torch.cuda.set_device(local)
     dev = f"cuda:{local}"
     stream = torch.cuda.current_stream(local)
-    sc = sg.district()
-    N, S, K, s = sc.n_facets, sc.n_snap, sc.max_order, sc.samples_per_side
-    W = ivm.words(N)
-    units = N * N + 2 * N * S   # the whole job's units (split across ranks when ws > 1)
-    rows = shard.row_ranges(N, ws)[rank]
-    snap_a, snap_b = shard.snapshot_ranges(S, ws)[rank]
     ctx = ivm.Context(local, stream)
-    facets_d = torch.from_numpy(sc.facets).to(dev)
-    tx_d = torch.from_numpy(sc.tx).to(dev)
-    rx_d = torch.from_numpy(sc.rx).to(dev)
-    M_d = torch.empty((N, W), dtype=torch.int32, device=dev)
-    T_d = torch.empty((S, 2, W), dtype=torch.int32, device=dev)
-    L_d = torch.empty((S,), dtype=torch.uint8, device=dev)
-    summ_d = torch.empty((S, K + 1, 3), dtype=torch.int64, device=dev)
-    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
-
-    forms = {
-        "plain": dict(mode=ivm.IVM_MODE_EXACT, flags=0),
-        "fast": dict(mode=ivm.IVM_MODE_FILTERED,
-                     flags=ivm.IVM_FLAG_PERSISTENT | ivm.IVM_FLAG_OCCLUDER_CACHE
-                     | ivm.IVM_FLAG_DEDUP_SOURCES | ivm.IVM_FLAG_GRAPH),
-    }
-
-    forms["learned"] = dict(mode=ivm.IVM_MODE_LEARNED, flags=forms["fast"]["flags"])
-
+    if args.profile:
+        profile_case(args, ivm, shard, sg, ctx, dev, stream)
+        ctx.close()
+        return
+    sc = sg.city()
+    fast = (ivm.IVM_FLAG_PERSISTENT | ivm.IVM_FLAG_OCCLUDER_CACHE | ivm.IVM_FLAG_DEDUP_SOURCES |
+            ivm.IVM_FLAG_GRAPH)
     # launch shape of the fast form from the library's autotuner (untimed)
-    tuned = ivm.ivm_autotune(ctx, facets_d, s, tx_d, rx_d, mode=forms["fast"]["mode"],
-                             flags=forms["fast"]["flags"])
-    shape = {"plain": ({}, {}),
-             "fast": ({"tile": tuned["tile"], "warps_per_block": tuned["warps_per_block"]},
-                      {"tile": tuned["table_tile"], "warps_per_block": tuned["warps_per_block"]})}
-    shape["learned"] = shape["fast"]
+    tuned = ivm.ivm_autotune(ctx, torch.from_numpy(sc.facets).to(dev), sc.samples_per_side,
+                             torch.from_numpy(sc.tx).to(dev), torch.from_numpy(sc.rx).to(dev),
+                             mode=ivm.IVM_MODE_FILTERED, flags=fast)
+    path = Path(ivm, shard, ctx, sc, dev, ws, rank, tuned, stream)
     # the cluster ranker of the learned form, trained (untimed) on the exact
     # method's logged hits in the tiny and degenerate scenes
     t0 = time.perf_counter()
     train_loss = ivm.ivm_ranker_train(ctx, [sg.tiny().facets, sg.degenerate(n_snap=16).facets],
-                                      s, epochs=12, lr=2e-3)
+                                      path.s, epochs=12, lr=2e-3)
     train_s = time.perf_counter() - t0
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
 
-    def step(form, fac, tx, rx, M, T, L, summ, marks=None):
-        """The three calls; `marks` (4 CUDA events) bracket them on the stream.
-        With ws > 1 this rank's share: its matrix rows, the all-reduce of the
-        parts, then the table and tree of its snapshot range."""
-        kw = forms[form]
-        kw_m, kw_t = shape[form]
-        if marks:
-            marks[0].record(stream)
-        if ws == 1:
-            _, stm = ivm.ivm_build_matrix(ctx, fac, s, out=M, **kw, **kw_m)
-        else:
-            _, stm = ivm.ivm_build_matrix_rows(ctx, fac, s, rows, out=M, **kw, **kw_m)
-            shard.exchange_matrix(M)
-        if marks:
-            marks[1].record(stream)
-        a, b = snap_a, snap_b
-        _, stt = ivm.ivm_build_table(ctx, fac, s, tx[a:b], rx[a:b], out=(T[a:b], L[a:b]),
-                                     **kw, **kw_t)
-        if marks:
-            marks[2].record(stream)
-        ivm.ivm_expand_image_tree(ctx, M, T[a:b], L[a:b], N, K, summary=summ[a:b])
-        if marks:
-            marks[3].record(stream)
-        return stm, stt
-
-    if args.profile:
-        # profiling case: one phase of one form (launch shape as timed), on the
-        # first --snapshots snapshots; the calls after the warm-up run inside
-        # the NVTX range "profile_<phase>" (ncu --nvtx --nvtx-include)
-        Sp = min(S, args.snapshots or S)
-        kw = forms[args.form]
-        kw_m, kw_t = shape[args.form]
-        st = None
-        for it in range(args.warmup + args.steps):
-            if it == args.warmup:
-                torch.cuda.synchronize()
-                torch.cuda.nvtx.range_push(f"profile_{args.profile}")
-            if args.profile in ("matrix", "step"):
-                _, st = ivm.ivm_build_matrix(ctx, facets_d, s, out=M_d, **kw, **kw_m)
-            if args.profile in ("table", "step"):
-                _, st = ivm.ivm_build_table(ctx, facets_d, s, tx_d[:Sp], rx_d[:Sp],
-                                            out=(T_d[:Sp], L_d[:Sp]), **kw, **kw_t)
-            if args.profile in ("tree", "step"):
-                if args.profile == "tree" and it == 0:
-                    ivm.ivm_build_matrix(ctx, facets_d, s, out=M_d, **kw, **kw_m)
-                    ivm.ivm_build_table(ctx, facets_d, s, tx_d[:Sp], rx_d[:Sp],
-                                        out=(T_d[:Sp], L_d[:Sp]), **kw, **kw_t)
-                ivm.ivm_expand_image_tree(ctx, M_d, T_d[:Sp], L_d[:Sp], N, K, summary=summ_d[:Sp])
-        torch.cuda.synchronize()
-        if args.steps:
-            torch.cuda.nvtx.range_pop()
-        if args.profile == "step":
-            st = None
-        print(json.dumps({"profile": args.profile, "form": args.form, "snapshots": Sp,
-                          "stats": st.as_dict() if st is not None else None}))
-        ctx.close()
-        return
-
-    def timed(form):
-        for _ in range(args.warmup):
-            step(form, facets_d, tx_d, rx_d, M_d, T_d, L_d, summ_d)
-        torch.cuda.synchronize()
-        barrier(ws)
-        torch.cuda.synchronize()
-        launches0 = ivm.kernel_launches()
-        times, kern = [], {"matrix": 0.0, "table": 0.0}
-        ops, node_tests, leaf_tests = {"matrix": 0, "table": 0}, 0, 0
-        calls = {"matrix": 0.0, "table": 0.0, "tree": 0.0}
-        stats = None
-        torch.cuda.nvtx.range_push(f"timed_{form}")
-        for _ in range(args.steps):
-            flush.zero_()
-            ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
-            stm, stt = step(form, facets_d, tx_d, rx_d, M_d, T_d, L_d, summ_d, marks=ev)
-            torch.cuda.synchronize()
-            times.append(ev[0].elapsed_time(ev[3]))
-            for k, name in enumerate(("matrix", "table", "tree")):
-                calls[name] += ev[k].elapsed_time(ev[k + 1]) / args.steps
-            kern["matrix"] += stm.ms_traverse
-            kern["table"] += stt.ms_traverse
-            for name, st in (("matrix", stm), ("table", stt)):
-                leaf_fp = st.leaf_tests - st.exact_tests if forms[form]["mode"] else 0
-                ops[name] += st.node_tests * FP32_OPS_PER_NODE_TEST + \
-                    leaf_fp * FP32_OPS_PER_FILTERED_LEAF
-            stats = (stm.as_dict(), stt.as_dict())
-        torch.cuda.nvtx.range_pop()
-        launches = ivm.kernel_launches() - launches0
-        torch.cuda.synchronize()
-        barrier(ws)
-        ms = max_over_ranks(ws, sum(times)) / args.steps
-        return ms, kern, ops, launches, stats, calls
-
-    clocks = Clocks(local)
-    ms_plain, kern_plain, ops_plain, _, stats_plain, calls_plain = timed("plain")
-    clocks.start()
-    ms_fast, kern_fast, ops_fast, launches, stats_fast, calls_fast = timed("fast")
-    clk = clocks.stop()
-    ms_lrn, kern_lrn, _, _, stats_lrn, calls_lrn = timed("learned")
-
-    # parity of the forms on this step's outputs (cheap, outside timing)
-    step("plain", facets_d, tx_d, rx_d, M_d, T_d, L_d, summ_d)
-    ref = (M_d.clone(), T_d.clone(), L_d.clone(), summ_d.clone())
-    step("fast", facets_d, tx_d, rx_d, M_d, T_d, L_d, summ_d)
-    forms_agree = all(bool((a == b).all()) for a, b in zip(ref, (M_d, T_d, L_d, summ_d)))
-    step("learned", facets_d, tx_d, rx_d, M_d, T_d, L_d, summ_d)
-    forms_agree &= all(bool((a == b).all()) for a, b in zip(ref, (M_d, T_d, L_d, summ_d)))
+    tf = timed(path, "fast", args.steps, args.warmup, flush, ws, clocks=Clocks(local))
+    # the plain and learned forms: fewer steps (plain takes about 12x longer)
+    tl = timed(path, "learned", min(args.steps, 5), min(args.warmup, 2), flush, ws)
+    tp = timed(path, "plain", min(args.steps, 2), min(args.warmup, 1), flush, ws)
+    agree = same_outputs(path, ["plain", "fast", "learned"])
+    N, S = path.N, path.S
+    units = path.units
+    value = units / (tf["ms"] / 1e3)
+    n_sm = torch.cuda.get_device_properties(local).multi_processor_count
 
     def per_seg(st, key):
         return st[key] / st["segments"] if st["segments"] else None
 
-    # visibility ranges, Blockage column and coherence time of this step's
-    # table (Sec. III-C/D), one call after the step, timed on its own
-    step("fast", facets_d, tx_d, rx_d, M_d, T_d, L_d, summ_d)
-    torch.cuda.synchronize()
-    rng_ms = []
-    for it in range(args.warmup + args.steps):
-        t0 = time.perf_counter()
-        recs, rsum = ivm.ivm_visibility_ranges(ctx, facets_d, s, tx_d[snap_a:snap_b],
-                                               rx_d[snap_a:snap_b], T_d[snap_a:snap_b])
-        if it >= args.warmup:
-            rng_ms.append(1e3 * (time.perf_counter() - t0))
-    dt_ms = 1.0   # snapshots are 1 ms apart (120 km/h, 10/3 cm per step)
-    tc = [dt_ms * rsum["snapshots"][x] / rsum["ranges"][x] if rsum["ranges"][x] else None
-          for x in range(2)]
-    ranges_out = {
-        "what": "visibility ranges (maximal runs of each table bit), first blocker at both ends "
-                "of each, coherence time per Eq. (8)-(9); C-ABI call ivm_visibility_ranges on "
-                "this step's table, records copied to host",
-        "ms_per_call": statistics.median(rng_ms),
-        "ranges": int(len(recs)),
-        "ranges_per_side": rsum["ranges"],
-        "snapshots_per_side": rsum["snapshots"],
-        "coherence_time_ms": {"tx": tc[0], "rx": tc[1],
-                              "scenario": min(x for x in tc if x is not None) if any(tc) else None},
-        "table_bits_per_s": 2 * N * (snap_b - snap_a) / (statistics.median(rng_ms) / 1e3),
-    }
-
-    # image-method validation of the step's image-tree candidates (Sec. IV-B),
-    # orders 0..2 at the first snapshots of this rank's range, timed on its own
-    ray_snaps, ray_K = min(4, snap_b - snap_a), 2
-    a0, a1 = snap_a, snap_a + ray_snaps
-    _, n_cand = ivm.ivm_expand_image_tree(ctx, M_d, T_d[a0:a1], L_d[a0:a1], N, ray_K,
-                                          count_paths=True)
-    _, cand, n_cand, _ = ivm.ivm_expand_image_tree(ctx, M_d, T_d[a0:a1], L_d[a0:a1], N, ray_K,
-                                                   paths_capacity=max(n_cand, 1))
-    cand = cand[:n_cand]
-    flags = torch.zeros(max(n_cand, 1), dtype=torch.uint8, device=dev)
-    ray_ms = []
-    for it in range(args.warmup + args.steps):
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        ivm.ivm_validate_paths(ctx, facets_d, s, tx_d[a0:a1], rx_d[a0:a1], cand, ray_K,
-                               out=flags[:n_cand])
-        if it >= args.warmup:
-            ray_ms.append(1e3 * (time.perf_counter() - t0))
-    n_valid = int(flags[:n_cand].sum().item()) if n_cand else 0
-    # edges as visible nodes and the edge nearest each source (Sec. III-B), timed on its own
-    E_d = torch.from_numpy(sg.edges_of(sc)).to(dev)
-    edge_ms = []
-    for it in range(args.warmup + args.steps):
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        etab, enear = ivm.ivm_build_edge_table(ctx, facets_d, s, E_d, tx_d[snap_a:snap_b],
-                                               rx_d[snap_a:snap_b], mode=ivm.IVM_MODE_FILTERED)
-        if it >= args.warmup:
-            edge_ms.append(1e3 * (time.perf_counter() - t0))
-    ebits = np.unpackbits(etab.view(np.uint8), axis=-1, bitorder="little")[..., :E_d.shape[0]]
-    edges_out = {
-        "what": "edge rows (the 8 convex edges of every building as visible nodes, s samples "
-                "each) and the nearest visible edge per source, C-ABI call ivm_build_edge_table, "
-                "results copied to host",
-        "edges": int(E_d.shape[0]), "ms_per_call": statistics.median(edge_ms),
-        "edge_tests_per_s": 2 * int(E_d.shape[0]) * (snap_b - snap_a) /
-                            (statistics.median(edge_ms) / 1e3),
-        "visible_edges_mean": [float(ebits[:, 0].sum(axis=1).mean()),
-                               float(ebits[:, 1].sum(axis=1).mean())],
-    }
-    # edges as matrix rows and columns: facet-edge and edge-edge visibility
-    # (Sec. I-II, Sec. III-B), timed on its own, outputs left on the device
-    EF_d = torch.from_numpy(sg.edge_faces_of(sc)).to(dev)
-    ne = int(E_d.shape[0])
-    fe_d = torch.zeros((N, (ne + 31) // 32), dtype=torch.int32, device=dev)
-    ee_d = torch.zeros((ne, (ne + 31) // 32), dtype=torch.int32, device=dev)
-    em_ms = []
-    for it in range(args.warmup + args.steps):
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        ivm.ivm_build_edge_matrix(ctx, facets_d, s, E_d, EF_d, out=(fe_d, ee_d))
-        if it >= args.warmup:
-            em_ms.append(1e3 * (time.perf_counter() - t0))
-    fe_bits = int(np.unpackbits(fe_d.cpu().numpy().view(np.uint8)).sum())
-    ee_bits = int(np.unpackbits(ee_d.cpu().numpy().view(np.uint8)).sum())
-    edge_matrix_out = {
-        "what": "edges as matrix rows and columns: facet-edge bits fe [N][WE] and edge-edge "
-                "bits ee [E][WE], C-ABI call ivm_build_edge_matrix, outputs on the device",
-        "facet_edge_pairs": N * ne, "edge_edge_pairs": ne * (ne - 1) // 2,
-        "ms_per_call": statistics.median(em_ms),
-        "pair_tests_per_s": (N * ne + ne * (ne - 1) // 2) / (statistics.median(em_ms) / 1e3),
-        "facet_edge_bits": fe_bits, "edge_edge_bits": ee_bits,
-    }
-    # interface relations and angular bouncing ranges of the step's visible
-    # pairs (Sec. II-B, Eq. (1)-(2)), timed on its own
-    rel_ms = []
-    for it in range(args.warmup + args.steps):
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        rpairs, rrel, _ = ivm.ivm_interface_relations(ctx, facets_d, s, M_d)
-        if it >= args.warmup:
-            rel_ms.append(1e3 * (time.perf_counter() - t0))
-    relations_out = {
-        "what": "PAR/PER relation and the four edges' angular bouncing ranges of every "
-                "visible ordered pair of the step's matrix, C-ABI call ivm_interface_relations, "
-                "results copied to host",
-        "pairs": int(len(rpairs)), "par": int((rrel == 1).sum()), "per": int((rrel == 2).sum()),
-        "ms_per_call": statistics.median(rel_ms),
-        "pairs_per_s": len(rpairs) / (statistics.median(rel_ms) / 1e3),
-    }
-    rays_out = {
-        "what": "image-method validation of image-tree candidates (orders 0-2) as specular "
-                f"rays, C-ABI call ivm_validate_paths, snapshots {a0}..{a1 - 1}",
-        "candidates": int(n_cand), "valid_rays": n_valid,
-        "ms_per_call": statistics.median(ray_ms),
-        "candidates_per_s": n_cand / (statistics.median(ray_ms) / 1e3) if ray_ms else None,
-    }
-
-    value = units / (ms_fast / 1e3)
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms_fast, "higher_is_better": True,
+        "warmup": args.warmup, "ms_per_step": tf["ms"], "higher_is_better": True,
         "scaling": "strong", "vs_baseline": None, "dtype": "int64/int128 + fp32 filter",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "form": "fast: FP32 filter + exact fallback, "
-                   "persistent work queue, occluder cache, one row per run of equal "
-                   "source positions, CUDA-graph replay of each call",
+        "config": {"workload": CITY,
+                   "form": "fast: FP32 filter + exact fallback, persistent work queue, occluder "
+                           "cache, one row per run of equal source positions, CUDA-graph replay "
+                           "of each call, launch shape from the autotuner",
                    "l2": "flushed between steps (512 MB write)",
-                   "facets": N, "snapshots": S, "samples_per_side": s, "max_order": K,
-                   "pair_tests_per_step": units, "autotuned_shape": tuned,
+                   "facets": N, "snapshots": S, "samples_per_side": path.s,
+                   "max_order": path.K, "pair_tests_per_step": units,
+                   "autotuned_shape": tuned,
                    "parallelism": "one workload split over ranks: matrix rows of about equal "
                                   "pair counts, one all-reduce of the matrix parts, snapshot "
                                   "ranges for the table and tree" if ws > 1 else "1 GPU"},
-        "snapshot_tables_per_s": S / (ms_fast / 1e3),
-        "plain": {"ms_per_step": ms_plain, "value": units / (ms_plain / 1e3),
-                  "form": "exact int64/int128 facet tests, one warp per work item"},
-        "speedup_vs_plain": ms_plain / ms_fast,
+        "snapshot_tables_per_s": S / (tf["ms"] / 1e3),
+        "ms_per_call": tf["calls"],
+        "plain": {"ms_per_step": tp["ms"], "value": units / (tp["ms"] / 1e3),
+                  "steps": tp["steps"], "warmup": tp["warmup"], "ms_per_call": tp["calls"],
+                  "form": "exact int64/int128 facet tests, one warp per work item, no caches"},
+        "speedup_vs_plain": tp["ms"] / tf["ms"],
         "learned": {
-            "form": "fast + learned cluster order in the matrix call (BF16 MLP ranking of "
-                    "64 BVH subtrees per candidate pair, tensor-core inference)",
-            "ms_per_step": ms_lrn, "value": units / (ms_lrn / 1e3),
-            "speedup_vs_plain": ms_plain / ms_lrn,
-            "matrix_ms_per_call": calls_lrn["matrix"],
-            "matrix_ms_per_call_without_ranker": calls_fast["matrix"],
-            "matrix_node_tests_per_segment": per_seg(stats_lrn[0], "node_tests"),
-            "matrix_node_tests_per_segment_without_ranker": per_seg(stats_fast[0], "node_tests"),
-            "matrix_leaf_tests_per_segment": per_seg(stats_lrn[0], "leaf_tests"),
-            "matrix_leaf_tests_per_segment_without_ranker": per_seg(stats_fast[0], "leaf_tests"),
-            "first_proposal_hits": stats_lrn[0]["ranker_hits"],
+            "form": "fast + learned cluster order in the matrix call (BF16 MLP ranking of 64 BVH "
+                    "subtrees per candidate pair, tensor-core inference)",
+            "ms_per_step": tl["ms"], "value": units / (tl["ms"] / 1e3),
+            "steps": tl["steps"], "warmup": tl["warmup"],
+            "speedup_vs_plain": tp["ms"] / tl["ms"],
+            "matrix_ms_per_call": tl["calls"]["matrix"],
+            "matrix_ms_per_call_without_ranker": tf["calls"]["matrix"],
+            "matrix_node_tests_per_segment": per_seg(tl["stats"]["matrix"], "node_tests"),
+            "matrix_node_tests_per_segment_without_ranker":
+                per_seg(tf["stats"]["matrix"], "node_tests"),
+            "matrix_leaf_tests_per_segment": per_seg(tl["stats"]["matrix"], "leaf_tests"),
+            "matrix_leaf_tests_per_segment_without_ranker":
+                per_seg(tf["stats"]["matrix"], "leaf_tests"),
+            "first_proposal_hits": tl["stats"]["matrix"]["ranker_hits"],
             "train": {"scenes": "tiny (41 facets) + degenerate district (1,001 facets)",
                       "epochs": 12, "final_loss": train_loss, "seconds": train_s}},
-        "ms_per_call": {"fast": calls_fast, "plain": calls_plain, "learned": calls_lrn},
-        "visibility_ranges": ranges_out,
-        "ray_validation": rays_out,
-        "edges": edges_out,
-        "edge_matrix": edge_matrix_out,
-        "interface_relations": relations_out,
-        "forms_bit_identical": forms_agree,
-        "gpu_launches": launches,
-        "clocks": clk,
-        "stats": {"matrix": stats_fast[0], "table": stats_fast[1]},
+        "forms_bit_identical": agree,
+        "gpu_launches": tf["launches"],
+        "clocks": tf["clocks"],
+        "stats": tf["stats"],
+        "roofline": roofline(tf, ivm, ctx, n_sm, "city"),
     }
-    # roofline of the dominant kernel (FP32 issue of the traversal)
-    dom = "table" if kern_fast["table"] >= kern_fast["matrix"] else "matrix"
-    kname = {"table": "k_table", "matrix": "k_matrix"}[dom]
-    import json as _json
-    peaks = _json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) \
-        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
-    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    n_sm = torch.cuda.get_device_properties(local).multi_processor_count
-    peak = n_sm * 128 * sm_max * 1e6 / 1e12
-    achieved = ops_fast[dom] / (kern_fast[dom] / 1e3) / 1e12 if kern_fast[dom] > 0 else 0.0
-    out["roofline"] = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak,
-                       "unit": "Tops/s", "frac": achieved / peak if peak else None,
-                       "traffic": traffic_from_profiles(kname),
-                       "peak_basis": f"{n_sm} SMs x 128 FP32 lanes x {sm_max:.0f} MHz "
-                                     "(sm_max_mhz of MEASURED_PEAKS.json)",
-                       "ms_per_launch": kern_fast[dom] / args.steps,
-                       "ms_per_step_matrix": kern_fast["matrix"] / args.steps,
-                       "ms_per_step_table": kern_fast["table"] / args.steps}
-    # the same fraction against this GPU's measured FMA issue rate (eight
-    # independent FMA chains per thread, full occupancy: ivm_fp32_peak)
-    ffma = ivm.ivm_fp32_peak(ctx) / 1e12
-    out["roofline"]["peak_measured_ffma"] = ffma
-    out["roofline"]["frac_of_measured_ffma"] = achieved / ffma if ffma else None
 
     if not args.no_e2e:
         fac_h = torch.from_numpy(sc.facets).pin_memory()
         tx_h = torch.from_numpy(sc.tx).pin_memory()
         rx_h = torch.from_numpy(sc.rx).pin_memory()
+        W, K = path.W, path.K
         M_h = torch.empty((N, W), dtype=torch.int32).pin_memory()
         T_h = torch.empty((S, 2, W), dtype=torch.int32).pin_memory()
         L_h = torch.empty((S,), dtype=torch.uint8).pin_memory()
         summ_h = torch.empty((S, K + 1, 3), dtype=torch.int64).pin_memory()
-        a, b = snap_a, snap_b
+        a, b = path.snap
 
         def e2e_step():
             if ws == 1:   # the library copies host buffers in and out itself
-                step("fast", fac_h, tx_h, rx_h, M_h, T_h, L_h, summ_h)
+                path.step("fast", bufs=(fac_h, tx_h, rx_h, M_h, T_h, L_h, summ_h))
                 return
             # the all-reduce needs device buffers: stage this rank's inputs and outputs
-            facets_d.copy_(fac_h, non_blocking=True)
-            tx_d[a:b].copy_(tx_h[a:b], non_blocking=True)
-            rx_d[a:b].copy_(rx_h[a:b], non_blocking=True)
-            step("fast", facets_d, tx_d, rx_d, M_d, T_d, L_d, summ_d)
-            M_h.copy_(M_d)
-            T_h[a:b].copy_(T_d[a:b])
-            L_h[a:b].copy_(L_d[a:b])
-            summ_h[a:b].copy_(summ_d[a:b])
+            path.fac.copy_(fac_h, non_blocking=True)
+            path.tx[a:b].copy_(tx_h[a:b], non_blocking=True)
+            path.rx[a:b].copy_(rx_h[a:b], non_blocking=True)
+            path.step("fast")
+            M_h.copy_(path.M)
+            T_h[a:b].copy_(path.T[a:b])
+            L_h[a:b].copy_(path.L[a:b])
+            summ_h[a:b].copy_(path.summ[a:b])
 
         for _ in range(max(1, args.warmup)):
             e2e_step()
@@ -597,7 +789,7 @@ def run_ours(args, ws, rank, local):
         torch.cuda.synchronize()
         e2e_s = max_over_ranks(ws, time.perf_counter() - t0) / args.steps
         Sr = b - a
-        if ws == 1:   # facets go in for both calls; the matrix goes out and back in
+        if ws == 1:   # facets go in for both calls; the matrix and table go out and back in
             h2d = 2 * fac_h.numel() * 4 + 2 * Sr * 3 * 4 + M_h.numel() * 4 + \
                 Sr * 2 * W * 4 + Sr
         else:
@@ -608,13 +800,19 @@ def run_ours(args, ws, rank, local):
                       "path": "same C-ABI calls with pinned host buffers" + (
                           "" if ws == 1 else ", staged through device buffers for the "
                           "all-reduce (rank 0's bytes)")}
+        del fac_h, tx_h, rx_h, M_h, T_h, L_h, summ_h
 
+    if rank == 0 and ws == 1:
+        out["precision"] = precision_block(ivm, sg, ctx, dev)
+        out["batch"] = batch_block(args, ivm, sg, ctx, dev, stream, flush)
+        out["district"] = district_block(args, ivm, shard, sg, ctx, dev, stream, flush)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         threads = os.cpu_count() or 1
-        u, dt = oracle_sample(sc, 32, 96, 7, threads)
+        u, dt = oracle_sample(sc, 48, 192, 7, threads, "grid")
         out["cpu_baseline"] = {"value": u / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
-                               "sample": "32 seeded matrix rows and 96 seeded snapshots of the "
-                                         f"district workload ({u} pair tests, {dt:.1f} s)"}
+                               "sample": "48 seeded matrix rows and 192 seeded snapshots of the "
+                                         f"city workload ({u} pair tests, {dt:.1f} s); "
+                                         + ORACLE_GRID}
     ctx.close()
     if rank == 0:
         print(json.dumps(out))

@@ -12,7 +12,8 @@ __int128).  A digest of the facet records, the samples per side and (for
 tables) the Tx/Rx positions is stored beside the bits, so a reader can tell
 when the scene generator has changed and the file is stale.  Run from the
 repository root: ``python tests/golden/make_oracle_matrices.py [matrix|table]``
-(the matrices take several minutes per scene on a few cores).
+(the matrices take several minutes per scene on a few cores).  The digest and
+the snapshot window are importable without loading the oracle.
 """
 import hashlib
 import os
@@ -24,7 +25,6 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
 
-import oracle  # noqa: E402
 from paper_2501_02747_gb300 import scenegen as sg  # noqa: E402
 
 SCENES = {"district": sg.district, "degenerate": sg.degenerate}
@@ -52,6 +52,7 @@ def grazing_window(sc):
 
 
 def write_matrices():
+    import oracle
     for name, make in SCENES.items():
         sc = make()   # default trajectory: it also places the degenerate buildings
         t0 = time.time()
@@ -63,6 +64,7 @@ def write_matrices():
 
 
 def write_tables():
+    import oracle
     sc = sg.degenerate()
     snaps = grazing_window(sc)
     t0 = time.time()
@@ -75,7 +77,6 @@ def write_tables():
 
 
 if __name__ == "__main__":
-    oracle.build()
     what = sys.argv[1:] or ["matrix", "table"]
     if "matrix" in what:
         write_matrices()

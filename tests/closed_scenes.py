@@ -44,6 +44,20 @@ def partial_blocker():
     return F(W1, W2, LOW), 4
 
 
+def point_sees_partly():
+    """The table's rule (Sec. III-A: a partly visible face is visible).  The
+    point X = (0, 50, 50) sees W2 (x = 1000, normal -x) past LOW (x = 500,
+    z in [0, 50]).  With s = 2, W2's samples sit at y, z in {25, 75}; the
+    segment from X crosses x = 500 at its midpoint, height (50 + z) / 2:
+    37.5 for z = 25 (inside LOW: blocked), 62.5 for z = 75 (free).  So 2 of
+    the 4 sample segments are free and the entry is 1; under an
+    all-samples rule it would be 0.  With BIG instead of LOW all 4 are
+    blocked and the entry is 0.
+    Returns (facets, X, blocked flags of the 4 samples in (y, z) order
+    (25,25), (25,75), (75,25), (75,75))."""
+    return F(W2, LOW), np.array([[0, 50, 50]], np.int32), [True, False, True, False]
+
+
 def back_facing():
     """W3 faces +x at x=1000: W1's samples (x=0) are behind it: M = 0."""
     return F(W1, W3), np.zeros((2, 2), int)

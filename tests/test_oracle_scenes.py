@@ -61,3 +61,21 @@ def test_los_same_point_and_open_air():
     assert list(los) == [1, 1]
     # a point between the walls sees both
     assert (bits(tab[:, 0, :], 2) == 1).all()
+
+
+def test_point_sees_a_partly_hidden_facet():
+    """Table entry of a facet whose samples are partly hidden from the point
+    (hand count: 2 of 4 free): 1 under the any-sample rule (Sec. III-A);
+    with a blocker covering all four segments: 0."""
+    F, X, want_blocked = cs.point_sees_partly()
+    s = 2
+    # W2's samples (scaled by 2s = 4): o = (1000, 100, 0), u = (0, -100, 0), v = (0, 0, 100)
+    samples = [(4 * 1000, 4 * y, 4 * z) for y in (25, 75) for z in (25, 75)]
+    P = 4 * X[0].astype(np.int64)
+    got = [oracle.blocked(F, s, P, np.array(q, np.int64)) for q in samples]
+    assert got == want_blocked
+    tab, _ = oracle.table(F, s, X, X)
+    assert bits(tab[:, 0, :], 2)[0].tolist() == [1, 0]     # W2 seen, LOW behind X
+    Fb = cs.F(cs.W2, cs.BIG)
+    tab, _ = oracle.table(Fb, s, X, X)
+    assert bits(tab[:, 0, :], 2)[0].tolist() == [0, 0]

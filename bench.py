@@ -72,10 +72,14 @@ def parse():
     # profiling case: one phase of one form on a slice of a workload (no JSON contract line)
     p.add_argument("--profile", choices=["matrix", "table", "tree", "step"], default=None)
     p.add_argument("--workload", choices=["city", "district"], default="city")
-    p.add_argument("--form", choices=["fast", "plain", "learned"], default="fast")
+    p.add_argument("--form", choices=["fast", "fast_edge_filter", "plain", "learned"],
+                   default="fast")
     p.add_argument("--snapshots", type=int, default=None)
     p.add_argument("--rows", type=int, default=None,
                    help="profiling: decide only the pairs of the first ROWS matrix rows")
+    p.add_argument("--shape", default=None,
+                   help="profiling: launch shape tile,warps_per_block,table_tile instead of "
+                        "the autotuner's")
     return p.parse_args()
 
 
@@ -249,15 +253,29 @@ def traffic_from_profiles(kernel):
 
 
 def fp32_flop(st):
-    """The method's FP32 work in one call's traversal, from its own counters:
-    box tests x 12 plus facet tests the FP32 filter decided x 50."""
-    return (st["node_tests"] * FLOP_PER_BOX_TEST +
-            max(st["leaf_tests"] - st["exact_tests"], 0) * FLOP_PER_FACET_TEST)
+    """The method's algorithmic FP32 work in one call's traversal, from its own
+    counters: box tests x 12 plus facet tests x 50."""
+    return st["node_tests"] * FLOP_PER_BOX_TEST + st["leaf_tests"] * FLOP_PER_FACET_TEST
 
 
 def popcount(a):
     import numpy as np
     return int(np.unpackbits(np.ascontiguousarray(a).view(np.uint8)).sum())
+
+
+def fast_flags(ivm):
+    """The fast form: persistent queues, occluder caches, row deduplication,
+    graph replay and the rectangle test for axis-aligned facets."""
+    return (ivm.IVM_FLAG_PERSISTENT | ivm.IVM_FLAG_OCCLUDER_CACHE | ivm.IVM_FLAG_DEDUP_SOURCES |
+            ivm.IVM_FLAG_GRAPH | ivm.IVM_FLAG_ALIGNED_FACETS)
+
+
+def runs(pos):
+    """Runs of equal consecutive positions in an [S][3] trajectory."""
+    import numpy as np
+    if len(pos) == 0:
+        return 0
+    return 1 + int((np.diff(pos, axis=0) != 0).any(axis=1).sum())
 
 
 class Path:
@@ -282,15 +300,20 @@ class Path:
         self.T = torch.empty((S, 2, self.W), dtype=torch.int32, device=dev)
         self.L = torch.empty((S,), dtype=torch.uint8, device=dev)
         self.summ = torch.empty((S, self.K + 1, 3), dtype=torch.int64, device=dev)
-        fast = (ivm.IVM_FLAG_PERSISTENT | ivm.IVM_FLAG_OCCLUDER_CACHE |
-                ivm.IVM_FLAG_DEDUP_SOURCES | ivm.IVM_FLAG_GRAPH)
+        fast = fast_flags(ivm)
         self.forms = {"plain": dict(mode=ivm.IVM_MODE_EXACT, flags=0),
                       "fast": dict(mode=ivm.IVM_MODE_FILTERED, flags=fast),
+                      "fast_edge_filter": dict(mode=ivm.IVM_MODE_FILTERED,
+                                               flags=fast & ~ivm.IVM_FLAG_ALIGNED_FACETS),
                       "learned": dict(mode=ivm.IVM_MODE_LEARNED, flags=fast)}
         self.tuned = tuned
         sm = {"tile": tuned["tile"], "warps_per_block": tuned["warps_per_block"]}
         stt = {"tile": tuned["table_tile"], "warps_per_block": tuned["warps_per_block"]}
-        self.shape = {"plain": ({}, {}), "fast": (sm, stt), "learned": (sm, stt)}
+        self.shape = {"plain": ({}, {}), "fast": (sm, stt), "fast_edge_filter": (sm, stt),
+                      "learned": (sm, stt)}
+        # rows the table actually traces: one per run of equal positions per side
+        self.traced = N * N + N * sum(runs(p) for p in (sc.tx[self.snap[0]:self.snap[1]],
+                                                        sc.rx[self.snap[0]:self.snap[1]]))
 
     def outputs(self):
         return (self.M, self.T, self.L, self.summ)
@@ -401,8 +424,9 @@ def roofline(t, ivm, ctx, n_sm, traffic_name):
             "peak_basis": f"nominal FP32: {n_sm} SMs x 128 lanes x 2 FLOP per FMA x "
                           f"{sm_max:.0f} MHz (sm_max_mhz of MEASURED_PEAKS.json)",
             "work_basis": f"{FLOP_PER_BOX_TEST} FLOP per segment-box test (node_tests) + "
-                          f"{FLOP_PER_FACET_TEST} FLOP per facet test decided in FP32 "
-                          "(leaf_tests - exact_tests), per launch",
+                          f"{FLOP_PER_FACET_TEST} FLOP per segment-facet test (leaf_tests), per "
+                          "launch: the method's tests counted by the library, each at the "
+                          "FLOP of its plain FP32 form",
             "ms_per_launch": ms, "flop_per_launch": t["flop"][dom],
             "node_tests": st["node_tests"], "leaf_tests": st["leaf_tests"],
             "exact_tests": st["exact_tests"], "segments": st["segments"],
@@ -415,15 +439,21 @@ def profile_case(args, ivm, shard, sg, ctx, dev, stream):
     """One phase of one form on a slice of a workload (launch shape as timed);
     the calls after the warm-up run inside the NVTX range "profile_<phase>"
     (ncu --nvtx --nvtx-include).  Prints the last call's counters."""
+    import dataclasses
+
     import torch
     sc = sg.city() if args.workload == "city" else sg.district()
-    fd = torch.from_numpy(sc.facets).to(dev)
     Sp = min(sc.n_snap, args.snapshots or sc.n_snap)
-    tx = torch.from_numpy(sc.tx[:Sp]).to(dev)
-    rx = torch.from_numpy(sc.rx[:Sp]).to(dev)
-    tuned = ivm.ivm_autotune(ctx, fd, sc.samples_per_side, tx, rx, mode=ivm.IVM_MODE_FILTERED,
-                             flags=ivm.IVM_FLAG_PERSISTENT | ivm.IVM_FLAG_OCCLUDER_CACHE |
-                             ivm.IVM_FLAG_DEDUP_SOURCES)
+    sc = dataclasses.replace(sc, tx=sc.tx[:Sp], rx=sc.rx[:Sp])   # buffers for the slice only
+    fd = torch.from_numpy(sc.facets).to(dev)
+    tx = torch.from_numpy(sc.tx).to(dev)
+    rx = torch.from_numpy(sc.rx).to(dev)
+    if args.shape:
+        t, w, tt = (int(x) for x in args.shape.split(","))
+        tuned = {"tile": t, "warps_per_block": w, "table_tile": tt}
+    else:
+        tuned = ivm.ivm_autotune(ctx, fd, sc.samples_per_side, tx, rx,
+                                 mode=ivm.IVM_MODE_FILTERED, flags=fast_flags(ivm))
     path = Path(ivm, shard, ctx, sc, dev, 1, 0, tuned, stream)
     if args.form == "learned":
         ivm.ivm_ranker_train(ctx, [sg.tiny().facets, sg.degenerate(n_snap=16).facets],
@@ -443,11 +473,9 @@ def profile_case(args, ivm, shard, sg, ctx, dev, stream):
             else:
                 _, st = ivm.ivm_build_matrix(ctx, fd, s, out=path.M, **kw, **kw_m)
         if args.profile in ("table", "step") or (args.profile == "tree" and it == 0):
-            _, st = ivm.ivm_build_table(ctx, fd, s, tx, rx, out=(path.T[:Sp], path.L[:Sp]),
-                                        **kw, **kw_t)
+            _, st = ivm.ivm_build_table(ctx, fd, s, tx, rx, out=(path.T, path.L), **kw, **kw_t)
         if args.profile in ("tree", "step"):
-            ivm.ivm_expand_image_tree(ctx, path.M, path.T[:Sp], path.L[:Sp], N, K,
-                                      summary=path.summ[:Sp])
+            ivm.ivm_expand_image_tree(ctx, path.M, path.T, path.L, N, K, summary=path.summ)
     torch.cuda.synchronize()
     if args.steps:
         torch.cuda.nvtx.range_pop()
@@ -470,8 +498,7 @@ def district_block(args, ivm, shard, sg, ctx, dev, stream, flush):
     fd = torch.from_numpy(sc.facets).to(dev)
     tuned = ivm.ivm_autotune(ctx, fd, sc.samples_per_side, torch.from_numpy(sc.tx).to(dev),
                              torch.from_numpy(sc.rx).to(dev), mode=ivm.IVM_MODE_FILTERED,
-                             flags=ivm.IVM_FLAG_PERSISTENT | ivm.IVM_FLAG_OCCLUDER_CACHE |
-                             ivm.IVM_FLAG_DEDUP_SOURCES | ivm.IVM_FLAG_GRAPH)
+                             flags=fast_flags(ivm))
     p = Path(ivm, shard, ctx, sc, dev, 1, 0, tuned, stream)
     tf = timed(p, "fast", args.steps, args.warmup, flush, 1)
     tp = timed(p, "plain", args.steps, args.warmup, flush, 1)
@@ -560,8 +587,8 @@ def precision_block(ivm, sg, ctx, dev):
     sc = sg.degenerate()
     s = sc.samples_per_side
     fd = torch.from_numpy(sc.facets).to(dev)
-    fast = (ivm.IVM_FLAG_PERSISTENT | ivm.IVM_FLAG_OCCLUDER_CACHE | ivm.IVM_FLAG_DEDUP_SOURCES |
-            ivm.IVM_FLAG_GRAPH)
+    # the four-edge FP32 filter on every facet (no rectangle test): the precision form
+    fast = fast_flags(ivm) & ~ivm.IVM_FLAG_ALIGNED_FACETS
     M, stm = ivm.ivm_build_matrix(ctx, fd, s, mode=ivm.IVM_MODE_FILTERED, flags=fast)
     (T, L), stt = ivm.ivm_build_table(ctx, fd, s, torch.from_numpy(sc.tx).to(dev),
                                       torch.from_numpy(sc.rx).to(dev),
@@ -571,7 +598,8 @@ def precision_block(ivm, sg, ctx, dev):
                        "placed degenerately (shared wall spans, aligned facades, equal "
                        "heights, vertical edges on Tx-Rx lines at snapshots "
                        f"{sc.meta['grazing_snapshots']}), 5x5 samples, 10,000 snapshots",
-           "form": "FP32 filter with exact int64/int128 fallback (+ persistent, caches, graph)"}
+           "form": "four-edge FP32 filter with a proven error bound on every facet test, exact "
+                   "int64/int128 fallback where it cannot decide (+ persistent, caches, graph)"}
     for name, st in (("matrix", stm.as_dict()), ("table", stt.as_dict())):
         out[name] = {"facet_tests": st["leaf_tests"], "undecided": st["undecided"],
                      "undecided_fraction": st["undecided"] / st["leaf_tests"]
@@ -607,8 +635,7 @@ def batch_block(args, ivm, sg, ctx, dev, stream, flush):
     fd = [torch.from_numpy(x.facets).to(dev) for x in scenes]
     tx = [torch.from_numpy(x.tx).to(dev) for x in scenes]
     rx = [torch.from_numpy(x.rx).to(dev) for x in scenes]
-    fast = (ivm.IVM_FLAG_PERSISTENT | ivm.IVM_FLAG_OCCLUDER_CACHE | ivm.IVM_FLAG_DEDUP_SOURCES |
-            ivm.IVM_FLAG_GRAPH)
+    fast = fast_flags(ivm)
     t0 = time.perf_counter()
     tuned = ivm.ivm_autotune(ctx, fd, s, tx, rx, mode=ivm.IVM_MODE_FILTERED, flags=fast)
     tune_s = time.perf_counter() - t0
@@ -680,8 +707,7 @@ def run_ours(args, ws, rank, local):
         ctx.close()
         return
     sc = sg.city()
-    fast = (ivm.IVM_FLAG_PERSISTENT | ivm.IVM_FLAG_OCCLUDER_CACHE | ivm.IVM_FLAG_DEDUP_SOURCES |
-            ivm.IVM_FLAG_GRAPH)
+    fast = fast_flags(ivm)
     # launch shape of the fast form from the library's autotuner (untimed)
     tuned = ivm.ivm_autotune(ctx, torch.from_numpy(sc.facets).to(dev), sc.samples_per_side,
                              torch.from_numpy(sc.tx).to(dev), torch.from_numpy(sc.rx).to(dev),
@@ -698,8 +724,9 @@ def run_ours(args, ws, rank, local):
     tf = timed(path, "fast", args.steps, args.warmup, flush, ws, clocks=Clocks(local))
     # the plain and learned forms: fewer steps (plain takes about 12x longer)
     tl = timed(path, "learned", min(args.steps, 5), min(args.warmup, 2), flush, ws)
+    te = timed(path, "fast_edge_filter", min(args.steps, 5), min(args.warmup, 2), flush, ws)
     tp = timed(path, "plain", min(args.steps, 2), min(args.warmup, 1), flush, ws)
-    agree = same_outputs(path, ["plain", "fast", "learned"])
+    agree = same_outputs(path, ["plain", "fast", "fast_edge_filter", "learned"])
     N, S = path.N, path.S
     units = path.units
     value = units / (tf["ms"] / 1e3)
@@ -714,9 +741,11 @@ def run_ours(args, ws, rank, local):
         "scaling": "strong", "vs_baseline": None, "dtype": "int64/int128 + fp32 filter",
         "data": "synthetic",
         "config": {"workload": CITY,
-                   "form": "fast: FP32 filter + exact fallback, persistent work queue, occluder "
-                           "cache, one row per run of equal source positions, CUDA-graph replay "
-                           "of each call, launch shape from the autotuner",
+                   "form": "fast: FP32 facet tests with proven error bounds (plane-crossing "
+                           "test for axis-aligned rectangles, four-edge filter otherwise) and "
+                           "exact fallback, persistent work queue, occluder cache, one row per "
+                           "run of equal source positions, CUDA-graph replay of each call, "
+                           "launch shape from the autotuner",
                    "l2": "flushed between steps (512 MB write)",
                    "facets": N, "snapshots": S, "samples_per_side": path.s,
                    "max_order": path.K, "pair_tests_per_step": units,
@@ -725,11 +754,22 @@ def run_ours(args, ws, rank, local):
                                   "pair counts, one all-reduce of the matrix parts, snapshot "
                                   "ranges for the table and tree" if ws > 1 else "1 GPU"},
         "snapshot_tables_per_s": S / (tf["ms"] / 1e3),
+        "traced_pair_tests_per_step": path.traced,
+        "value_traced": path.traced / (tf["ms"] / 1e3),
+        "units_note": "pair tests per step = N^2 matrix pairs + 2 N S table pairs; the Tx is "
+                      "static, so the table traces one Tx row and copies it over the route "
+                      "(row deduplication): traced_pair_tests_per_step counts one row per run "
+                      "of equal positions, value_traced is the rate on those",
         "ms_per_call": tf["calls"],
         "plain": {"ms_per_step": tp["ms"], "value": units / (tp["ms"] / 1e3),
                   "steps": tp["steps"], "warmup": tp["warmup"], "ms_per_call": tp["calls"],
                   "form": "exact int64/int128 facet tests, one warp per work item, no caches"},
         "speedup_vs_plain": tp["ms"] / tf["ms"],
+        "fast_edge_filter": {
+            "form": "the fast form with the four-edge FP32 filter on every facet (no rectangle "
+                    "test for axis-aligned facets)",
+            "ms_per_step": te["ms"], "value": units / (te["ms"] / 1e3), "steps": te["steps"],
+            "warmup": te["warmup"], "ms_per_call": te["calls"]},
         "learned": {
             "form": "fast + learned cluster order in the matrix call (BF16 MLP ranking of 64 BVH "
                     "subtrees per candidate pair, tensor-core inference)",

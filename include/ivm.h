@@ -80,6 +80,12 @@ extern "C" {
 #define IVM_FLAG_DEDUP_SOURCES 8  /* table: trace one row per run of equal positions */
 #define IVM_FLAG_NO_SPLIT 16      /* table, persistent: no lazy splitting of snapshot ranges
                                      (idle warps otherwise take half of a busy warp's rest) */
+#define IVM_FLAG_ALIGNED_FACETS 32 /* FILTERED / LEARNED: facets that are axis-aligned
+                                     rectangles (u and v along two different coordinate
+                                     axes) take a plane-crossing test, FP32 with a proven
+                                     error bound and exact int64 where it cannot decide,
+                                     in place of the four-edge FP32 filter; other facets
+                                     keep the filter.  Same bits; not in the paper */
 
 typedef struct ivm_facet {
     int32_t o[3], u[3], v[3]; /* cm; u x v points outward */

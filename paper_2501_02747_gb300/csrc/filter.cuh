@@ -139,4 +139,108 @@ struct FilteredLeaf {
     }
 };
 
+// ------------------------------------------------ axis-aligned rectangles
+//
+// For a facet whose normal lies along axis K and whose edges lie along the
+// other two axes (Leaf.dom bit 2), the open segment P -> P + d meets the
+// closed rectangle iff it crosses the plane x_K = O_K strictly between its
+// ends (an exact int32 sign test on sp = P_K - O_K and sp + d_K) at a point
+// inside the rectangle's closed range on both other axes m:
+//   c_lo = |sp| d_m - (lo_m - P_m) |d_K| >= 0  and  c_hi = (hi_m - P_m) |d_K| - |sp| d_m >= 0
+// (traverse.cuh, aligned_hit_k).  Each c = x - y is a difference of two
+// products of integers below 2^23, exact in float as factors.  With
+// x~ = fl(x), y~ = fl(y) (one rounding each, u = 2^-24) and c~ = fl(x~ - y~),
+//   |c~ - c| <= u |x~ - y~| + u (|x| + |y|) <= (2u + O(u^2)) (|x~| + |y~|),
+// so B = fl_up(|x~| + |y~|) 2^-22 (a power-of-two scaling, exact) bounds the
+// error with room to spare: c~ > B proves c > 0, c~ < -B proves c < 0.  When
+// some condition is not proven and none is proven false, the exact int64
+// test decides.  The products are round-to-nearest intrinsics, never
+// contracted into FMAs.
+
+// Exact int64 decision of the four conditions (the rare path), out of line.
+static __device__ __noinline__ bool aligned_settle(int a, int b, int d1, int d2, int lo1, int hi1,
+                                                   int lo2, int hi2)
+{
+    const long long t1 = (long long)a * d1, t2 = (long long)a * d2;
+    return ((long long)lo1 * b <= t1) & (t1 <= (long long)hi1 * b) & ((long long)lo2 * b <= t2) &
+           (t2 <= (long long)hi2 * b);
+}
+
+// 1 when x - y > 0 is proven, -1 when x - y < 0 is proven, 0 otherwise.
+__device__ __forceinline__ int diff_sign(float x, float y)
+{
+    const float c = __fsub_rn(x, y);
+    const float B = __fmul_rn(__fadd_ru(fabsf(x), fabsf(y)), 0x1p-22f);
+    return c > B ? 1 : (c < -B ? -1 : 0);
+}
+
+template <int K>
+__device__ __forceinline__ bool aligned_filtered_k(const Seg &s, const Leaf &L, WalkCounters &wc)
+{
+    constexpr int K1 = (K + 1) % 3, K2 = (K + 2) % 3;
+    const int P[3] = {s.px, s.py, s.pz}, D[3] = {s.dx, s.dy, s.dz};
+    const int O[3] = {L.ox, L.oy, L.oz};
+    const int E[3] = {L.ux + L.vx, L.uy + L.vy, L.uz + L.vz};   // far corner - O
+    const int sp = P[K] - O[K], sq = sp + D[K];
+    if ((sp > 0 && sq > 0) || (sp < 0 && sq < 0)) return false;
+    if (sp == 0 || sq == 0) {
+        if (sp != 0 || sq != 0) return false;   // touches the plane only at an endpoint
+        wc.exact++;
+        return coplanar_hit(s, L);
+    }
+    const int a = sp < 0 ? -sp : sp, b = D[K] < 0 ? -D[K] : D[K];
+    const int lo1 = min(O[K1], O[K1] + E[K1]) - P[K1], hi1 = max(O[K1], O[K1] + E[K1]) - P[K1];
+    const int lo2 = min(O[K2], O[K2] + E[K2]) - P[K2], hi2 = max(O[K2], O[K2] + E[K2]) - P[K2];
+    const float fa = (float)a, fb = (float)b;
+    const float x1 = __fmul_rn(fa, (float)D[K1]), x2 = __fmul_rn(fa, (float)D[K2]);
+    const int c0 = diff_sign(x1, __fmul_rn((float)lo1, fb));
+    const int c1 = diff_sign(__fmul_rn((float)hi1, fb), x1);
+    const int c2 = diff_sign(x2, __fmul_rn((float)lo2, fb));
+    const int c3 = diff_sign(__fmul_rn((float)hi2, fb), x2);
+    if ((c0 < 0) | (c1 < 0) | (c2 < 0) | (c3 < 0)) return false;
+    if ((c0 > 0) & (c1 > 0) & (c2 > 0) & (c3 > 0)) return true;
+    wc.undecided++;
+    wc.exact++;
+    return aligned_settle(a, b, D[K1], D[K2], lo1, hi1, lo2, hi2);
+}
+
+__device__ __forceinline__ bool aligned_filtered(const Seg &s, const Leaf &L, WalkCounters &wc)
+{
+    const int k = L.dom & 3;
+    if (k == 0) return aligned_filtered_k<0>(s, L, wc);
+    if (k == 1) return aligned_filtered_k<1>(s, L, wc);
+    return aligned_filtered_k<2>(s, L, wc);
+}
+
+// The filtered test with the rectangle form for axis-aligned facets
+// (IVM_FLAG_ALIGNED_FACETS), out of line with the register interface of
+// facet_hit_filtered_call: both tests give facet_hit_exact's answer.
+static __device__ __noinline__ int facet_hit_aligned_call(int px, int py, int pz, int dx, int dy,
+                                                          int dz, int ox, int oy, int oz, int ux,
+                                                          int uy, int uz, int vx, int vy, int vz,
+                                                          int nx, int ny, int nz, int dom)
+{
+    const Seg s = make_seg(px, py, pz, px + dx, py + dy, pz + dz);
+    Leaf L;
+    L.ox = ox; L.oy = oy; L.oz = oz; L.building = 0;
+    L.ux = ux; L.uy = uy; L.uz = uz; L.scene = 0;
+    L.vx = vx; L.vy = vy; L.vz = vz; L.dom = dom;
+    L.nx = nx; L.ny = ny; L.nz = nz; L.pad = 0;
+    WalkCounters wc;
+    const bool hit = (dom & 4) ? aligned_filtered(s, L, wc) : facet_hit_filtered(s, L, wc);
+    return (int)hit | ((wc.exact != 0) << 1) | ((wc.undecided != 0) << 2);
+}
+
+struct AlignedLeafCall {
+    __device__ __forceinline__ bool operator()(const Seg &s, const Leaf &L, WalkCounters &wc) const
+    {
+        const int r = facet_hit_aligned_call(s.px, s.py, s.pz, s.dx, s.dy, s.dz, L.ox, L.oy, L.oz,
+                                             L.ux, L.uy, L.uz, L.vx, L.vy, L.vz, L.nx, L.ny,
+                                             L.nz, L.dom);
+        wc.exact += (r >> 1) & 1;
+        wc.undecided += (r >> 2) & 1;
+        return r & 1;
+    }
+};
+
 }  // namespace ivm

@@ -2,8 +2,9 @@
 // stage, Sec. III-C: vertex positions and face IDs of every building).
 //
 // Per facet: check the range contract, scale by 2s, reduce the outward
-// normal u x v by the gcd of its components, record its bounding box, and
-// write the s x s cell-centre samples p_ab = 2s o + (2a+1) u + (2b+1) v.
+// normal u x v by the gcd of its components, mark axis-aligned rectangles,
+// record its bounding box, and write the s x s cell-centre samples
+// p_ab = 2s o + (2a+1) u + (2b+1) v.
 #include "ivm_internal.cuh"
 
 namespace ivm {
@@ -72,6 +73,13 @@ __global__ void k_ingest(DevScenes g, int *err)
     int dom = 0;
     if (llabs_(nr[1]) > llabs_(nr[dom])) dom = 1;
     if (llabs_(nr[2]) > llabs_(nr[dom])) dom = 2;
+    // axis-aligned rectangle: U and V each along one coordinate axis, not the same one
+    int nu = 0, nv = 0, au = -1, av = -1;
+    for (int a = 0; a < 3; a++) {
+        if (u[a]) { nu++; au = a; }
+        if (v[a]) { nv++; av = a; }
+    }
+    if (nu == 1 && nv == 1 && au != av) dom |= 4;
     Leaf L;
     L.ox = (int)(k * o[0]); L.oy = (int)(k * o[1]); L.oz = (int)(k * o[2]);
     L.building = r.building;

@@ -170,6 +170,7 @@ LaunchCfg launch_cfg(const ivm_ctx *c, const ivm_params *p)
     L.n_sm = c->n_sm;
     L.cache = (p->flags & IVM_FLAG_OCCLUDER_CACHE) != 0;
     L.dedup = (p->flags & IVM_FLAG_DEDUP_SOURCES) != 0;
+    L.aligned = (p->flags & IVM_FLAG_ALIGNED_FACETS) != 0;
     return L;
 }
 

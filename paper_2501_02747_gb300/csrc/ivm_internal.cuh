@@ -24,7 +24,8 @@ __device__ __forceinline__ void raise_error(int *err, int code) { atomicCAS(err,
 struct __align__(16) Leaf {
     int ox, oy, oz, building;   // origin O = 2s o
     int ux, uy, uz, scene;      // edge U = 2s u
-    int vx, vy, vz, dom;        // edge V = 2s v; dom = dominant axis of n
+    int vx, vy, vz, dom;        // edge V = 2s v; dom: bits 0-1 the dominant axis of n,
+                                // bit 2 set when U and V lie along two different axes
     int nx, ny, nz, pad;        // reduced outward normal; pad = Morton-sorted position
 };
 
@@ -130,6 +131,7 @@ struct LaunchCfg {
     int n_sm;
     int cache;            // occluder cache in front of the BVH walk
     int dedup;            // table: compute one row per run of equal source positions
+    int aligned = 0;      // filtered forms: exact test for axis-aligned rectangle facets
     const unsigned long long *count_dev = nullptr;  // matrix, persistent: device pair count
     LearnedDev learn;     // matrix, learned form (ranks == nullptr: off)
     void *steal = nullptr;// table, persistent: 16-byte slots, 64 per SM (nullptr: no splitting)

@@ -635,7 +635,10 @@ __device__ __forceinline__ void los_item(const DevScenes &g, long long chunk, in
 // sweep of 4-8 on the district gave the same times at fixed launch shapes
 // (the kernel is bound by its work items' latency, not by resident warps),
 // and 4 keeps the per-snapshot state in registers (8 spills 1.5 KB a thread).
-constexpr int kTableMinBlocks = 4;
+#ifndef IVM_TABLE_MIN_BLOCKS
+#define IVM_TABLE_MIN_BLOCKS 4
+#endif
+constexpr int kTableMinBlocks = IVM_TABLE_MIN_BLOCKS;
 
 // A warp whose queue is empty: take the back half of the largest remaining
 // range (at least two stretches) in a window of slots, do it, and look again;
@@ -861,6 +864,8 @@ cudaError_t launch_table(const DevScenes &g, long long total_snap, long long tot
     const int *r = cfg.dedup ? rep : nullptr;
     if (cfg.mode == IVM_MODE_EXACT)
         launch_leaf<ExactLeaf>(g, total_items, all, snap_tile, cfg, r, work, ctr, err, st);
+    else if (cfg.aligned)
+        launch_leaf<AlignedLeafCall>(g, total_items, all, snap_tile, cfg, r, work, ctr, err, st);
     else
         launch_leaf<FilteredLeafCall>(g, total_items, all, snap_tile, cfg, r, work, ctr, err, st);
     if (cfg.dedup && total_snap > 0) {

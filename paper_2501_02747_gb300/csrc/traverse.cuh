@@ -100,6 +100,7 @@ static __device__ __noinline__ bool coplanar_clip_v(int px, int py, int pz, int 
                                                     int vx, int vy, int vz, int dom,
                                                     long long *lo_num, long long *lo_den)
 {
+    dom &= 3;   // bit 2 marks axis-aligned rectangles
     int a0 = dom == 0 ? 1 : 0;
     int a1 = dom == 2 ? 1 : 2;
     auto pick = [](int x, int y, int z, int a) { return a == 0 ? x : (a == 1 ? y : z); };
@@ -166,6 +167,43 @@ __device__ __forceinline__ bool facet_hit_exact(const Seg &s, const Leaf &L)
     bool nonneg = (e0 >= 0) & (e1 >= 0) & (e2 >= 0) & (e3 >= 0);
     bool nonpos = (e0 <= 0) & (e1 <= 0) & (e2 <= 0) & (e3 <= 0);
     return nonneg | nonpos;
+}
+
+// Exact test for an axis-aligned rectangle facet (normal along axis K, U and V
+// along the other two axes): the same answer as facet_hit_exact.  The open
+// segment P -> P + d meets the closed rectangle when P and P + d lie strictly
+// on opposite sides of the plane x_K = O_K and the crossing point lies in the
+// rectangle's closed range on both other axes; with sp = P_K - O_K the
+// crossing is at P + (|sp| / |d_K|) d, so on axis m the condition is
+//   (lo_m - P_m) |d_K| <= |sp| d_m <= (hi_m - P_m) |d_K|,
+// products of integers below 2^23 in magnitude, exact in int64.  A segment
+// in the plane goes to the coplanar clip; touching the plane at one end only
+// is no hit (open segment).
+template <int K>
+__device__ __forceinline__ bool aligned_hit_k(const Seg &s, const Leaf &L)
+{
+    constexpr int K1 = (K + 1) % 3, K2 = (K + 2) % 3;
+    const int P[3] = {s.px, s.py, s.pz}, D[3] = {s.dx, s.dy, s.dz};
+    const int O[3] = {L.ox, L.oy, L.oz};
+    const int E[3] = {L.ux + L.vx, L.uy + L.vy, L.uz + L.vz};   // far corner - O
+    const int sp = P[K] - O[K], sq = sp + D[K];
+    if ((sp > 0 && sq > 0) || (sp < 0 && sq < 0)) return false;
+    if (sp == 0 || sq == 0) return (sp == 0 && sq == 0) ? coplanar_hit(s, L) : false;
+    const long long a = sp < 0 ? -sp : sp, b = D[K] < 0 ? -D[K] : D[K];
+    const int lo1 = min(O[K1], O[K1] + E[K1]) - P[K1], hi1 = max(O[K1], O[K1] + E[K1]) - P[K1];
+    const int lo2 = min(O[K2], O[K2] + E[K2]) - P[K2], hi2 = max(O[K2], O[K2] + E[K2]) - P[K2];
+    const long long t1 = a * D[K1], t2 = a * D[K2];
+    return ((long long)lo1 * b <= t1) & (t1 <= (long long)hi1 * b) & ((long long)lo2 * b <= t2) &
+           (t2 <= (long long)hi2 * b);
+}
+
+// The facet test for facets marked axis-aligned (Leaf.dom bit 2).
+__device__ __forceinline__ bool aligned_hit(const Seg &s, const Leaf &L)
+{
+    const int k = L.dom & 3;
+    if (k == 0) return aligned_hit_k<0>(s, L);
+    if (k == 1) return aligned_hit_k<1>(s, L);
+    return aligned_hit_k<2>(s, L);
 }
 
 // Strict facing test: (u x v) . (x - O) > 0, exact in int64 (|n| < 2^31).

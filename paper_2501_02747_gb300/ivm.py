@@ -20,6 +20,7 @@ IVM_ERR_TIMEOUT, IVM_ERR_CUDA, IVM_ERR_INTERNAL = 4, 5, 6
 IVM_MODE_EXACT, IVM_MODE_FILTERED, IVM_MODE_LEARNED = 0, 1, 2
 IVM_FLAG_PERSISTENT, IVM_FLAG_GRAPH, IVM_FLAG_OCCLUDER_CACHE, IVM_FLAG_DEDUP_SOURCES = 1, 2, 4, 8
 IVM_FLAG_NO_SPLIT = 16
+IVM_FLAG_ALIGNED_FACETS = 32
 
 
 class ivm_facet(ctypes.Structure):

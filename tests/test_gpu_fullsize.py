@@ -32,8 +32,10 @@ from tests.gpu_common import padding_is_zero, to_np, unpack
 
 pytestmark = pytest.mark.gpu
 
+# the benchmark's fast form
 FAST = (ivm.IVM_FLAG_PERSISTENT | ivm.IVM_FLAG_OCCLUDER_CACHE | ivm.IVM_FLAG_DEDUP_SOURCES |
-        ivm.IVM_FLAG_GRAPH)
+        ivm.IVM_FLAG_GRAPH | ivm.IVM_FLAG_ALIGNED_FACETS)
+EDGE_FILTER = FAST & ~ivm.IVM_FLAG_ALIGNED_FACETS & ~ivm.IVM_FLAG_GRAPH
 
 
 @pytest.fixture(scope="module")
@@ -101,7 +103,7 @@ def district_family(request, ctx):
 def test_district_family_every_bit(ctx, district_family):
     name, sc, Mo, To, Lo = district_family
     s, n = sc.samples_per_side, sc.n_facets
-    for mode, flags in ((ivm.IVM_MODE_EXACT, 0), (ivm.IVM_MODE_FILTERED, FAST & ~ivm.IVM_FLAG_GRAPH)):
+    for mode, flags in ((ivm.IVM_MODE_EXACT, 0), (ivm.IVM_MODE_FILTERED, EDGE_FILTER)):
         M, _ = ivm.ivm_build_matrix(ctx, sc.facets, s, mode=mode, flags=flags)
         (T, L), _ = ivm.ivm_build_table(ctx, sc.facets, s, sc.tx, sc.rx, mode=mode, flags=flags)
         assert (to_np(M) == Mo).all(), (name, mode)
@@ -118,7 +120,8 @@ def test_degenerate_rows_around_grazing_snapshots_equal_brute_force(ctx):
     snaps = grazing_window(sc)
     assert set(sc.meta["grazing_snapshots"]) <= set(snaps.tolist())
     assert str(z["digest"]) == digest(sc.facets, 5, sc.tx[snaps], sc.rx[snaps])
-    for mode, flags in ((ivm.IVM_MODE_EXACT, 0), (ivm.IVM_MODE_FILTERED, FAST)):
+    for mode, flags in ((ivm.IVM_MODE_EXACT, 0), (ivm.IVM_MODE_FILTERED, EDGE_FILTER),
+                        (ivm.IVM_MODE_FILTERED, FAST)):
         (T, L), _ = ivm.ivm_build_table(ctx, sc.facets, 5, sc.tx, sc.rx, mode=mode, flags=flags)
         assert (to_np(T)[snaps] == z["table"]).all() and (L.cpu().numpy()[snaps] == z["los"]).all()
 

@@ -17,8 +17,9 @@ pytestmark = pytest.mark.gpu
 
 MODES = [ivm.IVM_MODE_EXACT, ivm.IVM_MODE_FILTERED]
 FAST = ivm.IVM_FLAG_PERSISTENT | ivm.IVM_FLAG_OCCLUDER_CACHE | ivm.IVM_FLAG_DEDUP_SOURCES
+ALIGNED = ivm.IVM_FLAG_ALIGNED_FACETS
 FLAG_SETS = [0, ivm.IVM_FLAG_PERSISTENT, ivm.IVM_FLAG_OCCLUDER_CACHE,
-             ivm.IVM_FLAG_DEDUP_SOURCES, FAST]
+             ivm.IVM_FLAG_DEDUP_SOURCES, FAST, ALIGNED, FAST | ALIGNED]
 
 
 @pytest.fixture(scope="module")
@@ -84,7 +85,7 @@ def test_random_small_scenes_full(ctx, seed, nb, s):
     want = oracle.matrix(sc.facets, s)
     tab, los = oracle.table(sc.facets, s, sc.tx, sc.rx)
     for mode in MODES:
-        for flags in (0, FAST):
+        for flags in (0, FAST, FAST | ALIGNED):
             M, _ = gpu_matrix(ctx, sc.facets, s, mode, flags)
             assert (M == want).all(), (mode, flags)
             assert padding_is_zero(M, sc.n_facets)
@@ -351,3 +352,39 @@ def test_degenerate_filtered_equals_exact_and_oracle(ctx):
     snaps = list(rng.choice(S, 3, replace=False))
     tab, los = oracle.table(sc.facets, 5, sc.tx, sc.rx, snaps=snaps)
     assert (T[snaps] == tab).all() and (L[snaps] == los).all()
+
+
+def rotated_box_facets(cx, cy, a, b, h, ux, uy, building):
+    """Roof and walls of a box whose footprint edges run along (ux, uy) and
+    (-uy, ux) (integer direction, not axis-aligned), u x v outward."""
+    ex, ey = ux * a, uy * a            # first footprint edge
+    fx, fy = -uy * b, ux * b           # second footprint edge
+    x0, y0 = cx - (ex + fx) // 2, cy - (ey + fy) // 2
+    c = [(x0, y0), (x0 + ex, y0 + ey), (x0 + ex + fx, y0 + ey + fy), (x0 + fx, y0 + fy)]
+    rows = [(x0, y0, h, ex, ey, 0, fx, fy, 0, building)]          # roof: e x f is +z
+    for k in range(4):
+        (px, py), (qx, qy) = c[k], c[(k + 1) % 4]
+        rows.append((px, py, 0, qx - px, qy - py, 0, 0, 0, h, building))
+    return rows
+
+
+def test_aligned_fast_path_with_slanted_facets(ctx):
+    """IVM_FLAG_ALIGNED_FACETS on a scene mixing axis-aligned boxes with boxes
+    turned off the axes (their walls and roofs keep the FP32 filter): every
+    bit equals the oracle's, in both forms that take the flag."""
+    sc = sg.random_small_city(461, n_buildings=5, side=9000, n_snap=30, s=3)
+    extra = rotated_box_facets(2500, 6500, 3, 2, 1700, 300, 400, 90) + \
+        rotated_box_facets(7000, 2500, 4, 3, 900, 500, -200, 91)
+    F = np.concatenate([sc.facets, np.asarray(extra, dtype=np.int32)])
+    for row, ctr in zip(extra, [(2500, 6500, 850)] * 5 + [(7000, 2500, 450)] * 5):
+        o, u, v = np.array(row[0:3]), np.array(row[3:6]), np.array(row[6:9])
+        assert np.cross(u, v) @ (o + (u + v) / 2 - np.array(ctr)) > 0   # outward
+    want = oracle.matrix(F, 3)
+    tab, los = oracle.table(F, 3, sc.tx, sc.rx)
+    for mode in (ivm.IVM_MODE_FILTERED, ivm.IVM_MODE_LEARNED):
+        for flags in (ALIGNED, FAST | ALIGNED):
+            M, _ = gpu_matrix(ctx, F, 3, mode, flags)
+            assert (M == want).all(), (mode, flags)
+            T, L, _ = gpu_table(ctx, F, 3, sc.tx, sc.rx, mode, flags)
+            assert (T == tab).all() and (L == los).all(), (mode, flags)
+    assert unpack(want, F.shape[0])[sc.n_facets:].sum() > 0       # the slanted facets see

@@ -193,20 +193,32 @@ def test_learned_batched_scenes(trained, fresh_ctx):
         assert (to_np(M) == oracle.matrix(F, 2)).all()
 
 
-def test_ranker_gain_is_reported(trained, fresh_ctx):
-    """Work per blocked-candidate segment with and without the trained ranker
-    on the district (printed; the verdicts are identical either way)."""
+def test_trained_ranker_cuts_the_walks(trained, fresh_ctx):
+    """What the trained network gains over the method without it, on the
+    district's matrix: the walks test at least 5 % fewer BVH boxes per
+    segment with the trained ranker than without one, and fewer than with
+    random weights of the same shape; the bits are identical in all three
+    cases.  (The time of the call
+    is reported by the benchmark: the ranking pass costs more than the shorter
+    walks save.)  Without the occluder cache every segment walks, so the three
+    runs test the same segments."""
     _, _, blob = trained
     sc = sg.district(n_snap=16)
+    flags = ivm.IVM_FLAG_PERSISTENT
     Mf, sf = ivm.ivm_build_matrix(fresh_ctx, sc.facets, 5, mode=ivm.IVM_MODE_FILTERED,
-                                  flags=ivm.IVM_FLAG_PERSISTENT)
+                                  flags=flags)
     ivm.ivm_ranker_load(fresh_ctx, blob)
     Ml, sl = ivm.ivm_build_matrix(fresh_ctx, sc.facets, 5, mode=ivm.IVM_MODE_LEARNED,
-                                  flags=ivm.IVM_FLAG_PERSISTENT)
-    assert (to_np(Mf) == to_np(Ml)).all()
-    assert sl.segments == sf.segments and sl.cand_pairs == sf.cand_pairs
-    assert sl.ranker_hits > 0
-    print(f"\nfiltered: node {sf.node_tests / sf.segments:.2f} leaf {sf.leaf_tests / sf.segments:.2f}"
-          f" per segment, {sf.ms_traverse:.3f} ms; learned: node {sl.node_tests / sl.segments:.2f}"
-          f" leaf {sl.leaf_tests / sl.segments:.2f}, {sl.ms_traverse:.3f} ms,"
-          f" first-proposal hits {sl.ranker_hits}")
+                                  flags=flags)
+    ivm.ivm_ranker_load(fresh_ctx, blob_of(he_weights(np.random.default_rng(8))))
+    Mr, sr = ivm.ivm_build_matrix(fresh_ctx, sc.facets, 5, mode=ivm.IVM_MODE_LEARNED,
+                                  flags=flags)
+    assert (to_np(Mf) == to_np(Ml)).all() and (to_np(Mf) == to_np(Mr)).all()
+    assert sl.segments == sf.segments == sr.segments and sl.ranker_hits > 0
+    per_seg = {k: st.node_tests / st.segments for k, st in
+               (("plain walk", sf), ("trained", sl), ("random", sr))}
+    print("\nnode tests per segment:", {k: round(v, 3) for k, v in per_seg.items()},
+          f"first-proposal hits: trained {sl.ranker_hits}, random {sr.ranker_hits}")
+    assert per_seg["trained"] <= 0.95 * per_seg["plain walk"]
+    assert per_seg["trained"] < per_seg["random"]
+    assert sl.ranker_hits > sr.ranker_hits

@@ -1560,8 +1560,8 @@ extern "C" int ivm_autotune(ivm_ctx *c, const ivm_scene *scenes, int32_t n_scene
     ivm_params base = *params;
     base.flags &= ~IVM_FLAG_GRAPH;
     const int wpbs[] = {2, 4};
-    const int mtiles[] = {1, 2, 4, 8, 16};
-    const int ttiles[] = {8, 16, 32, 64, 128, 256};
+    const int mtiles[] = {1, 2, 4, 8, 16, 32, 64};
+    const int ttiles[] = {8, 16, 32, 64, 128, 256, 512, 1024, 2048};
     float best_total = 1e30f;
     ivm_params best = *params;
     for (int wpb : wpbs) {

@@ -168,13 +168,15 @@ __device__ __forceinline__ void decide_pair(const DevScenes &g, int gi, int gj,
 
 // Register cap of the matrix kernel: 8 resident blocks of 128 threads (64
 // registers; a sweep of 3-12 blocks on the district and the city: more warps
-// hide the dependent box-test latency better than the spills cost).  The
-// learned walk holds more state and keeps 4.
+// hide the dependent box-test latency better than the spills cost; 10 and 12
+// were slower again with the out-of-line facet test).  The learned walk
+// holds more state: 6 (city, learned form: 417 ms against 445 ms with 4 and
+// 449 ms with 8).
 #ifndef IVM_MATRIX_MIN_BLOCKS
 #define IVM_MATRIX_MIN_BLOCKS 8
 #endif
 #ifndef IVM_MATRIX_MIN_BLOCKS_LEARNED
-#define IVM_MATRIX_MIN_BLOCKS_LEARNED 4
+#define IVM_MATRIX_MIN_BLOCKS_LEARNED 6
 #endif
 constexpr int kMatrixMinBlocks = IVM_MATRIX_MIN_BLOCKS,
               kMatrixMinBlocksLearned = IVM_MATRIX_MIN_BLOCKS_LEARNED;

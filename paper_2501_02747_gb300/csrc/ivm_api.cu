@@ -576,7 +576,8 @@ int build_matrix(ivm_ctx *c, const ivm_scene *scenes, int32_t n_scenes, const iv
             CK(ranker_clusters(g, ptr<int>(c, S_CBOX), ptr<signed char>(c, S_NCL), c->stream));
             CK(ranker_rank_pairs(g, ptr<int2>(c, S_PAIRS), npairs, cfg.count_dev,
                                  ptr<int>(c, S_CBOX), RankerDev{c->r_wt, c->r_master},
-                                 ptr<unsigned long long>(c, S_RANKS), c->n_sm, c->stream));
+                                 ptr<unsigned long long>(c, S_RANKS), c->n_sm, c->d_err,
+                                 c->stream));
             cfg.learn.ranks = ptr<unsigned long long>(c, S_RANKS);
             cfg.learn.ctx = ptr<int>(c, S_CBOX);
             cfg.learn.ncl = ptr<signed char>(c, S_NCL);
@@ -1474,8 +1475,11 @@ extern "C" int ivm_ranker_infer(ivm_ctx *c, const float *x, int32_t batch, float
     if ((r = ensure(c, S_RANKS, sizeof(unsigned long long) * (size_t)batch))) return r;
     CK(cudaMemcpyAsync(ptr<float>(c, S_RXB), x, sizeof(float) * (size_t)batch * kRIn,
                        cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
     CK(ranker_infer(ptr<float>(c, S_RXB), (unsigned long long)batch, RankerDev{c->r_wt, c->r_master},
-                    ptr<float>(c, S_RACT), ptr<unsigned long long>(c, S_RANKS), c->n_sm, c->stream));
+                    ptr<float>(c, S_RACT), ptr<unsigned long long>(c, S_RANKS), c->n_sm, c->d_err,
+                    c->stream));
+    if ((r = read_error(c))) return r;
     if (logits)
         CK(cudaMemcpyAsync(logits, ptr<float>(c, S_RACT), sizeof(float) * (size_t)batch * kROut,
                            cudaMemcpyDeviceToHost, c->stream));

@@ -132,6 +132,15 @@ __global__ void k_cbox(DevScenes g, int *ctx)
     }
 }
 
+__global__ void k_cbox_float(int *ctx, int n_scenes)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_scenes * 6 * kRClusters) return;
+    int *C = ctx + (size_t)kRCtx * (i / (6 * kRClusters));
+    const int k = i % (6 * kRClusters);
+    C[kRCFBox + k] = __float_as_int(2.f * (float)C[kRCBox + k]);
+}
+
 cudaError_t ranker_clusters(const DevScenes &g, int *ctx, signed char *ncl, cudaStream_t st)
 {
     cudaError_t e;
@@ -142,230 +151,369 @@ cudaError_t ranker_clusters(const DevScenes &g, int *ctx, signed char *ncl, cuda
     const int n = 6 * kRClusters * g.n_scenes;
     k_cbox_init<<<(n + 255) / 256, 256, 0, st>>>(ctx, g.n_scenes);
     k_cbox<<<(g.total_facets + 255) / 256, 256, 0, st>>>(g, ctx);
-    note_launches(3);
+    k_cbox_float<<<(n + 255) / 256, 256, 0, st>>>(ctx, g.n_scenes);
+    note_launches(4);
     return cudaGetLastError();
 }
 
 // ------------------------------------------------------------ inference
 
-__device__ __forceinline__ void mma_bf16(float *c, unsigned a0, unsigned a1, unsigned a2,
-                                         unsigned a3, unsigned b0, unsigned b1)
+// tcgen05 (5th-generation tensor cores) in inline PTX.  One CTA per SM holds
+// the BF16 weights of all four layers in shared memory (100 KB) and 128
+// columns of tensor memory (TMEM) for the accumulator; it takes tiles of 128
+// candidate pairs (M = 128, one TMEM lane per pair).  Per tile: the features
+// go to shared memory as the A operand of layer 1; thread 0 issues the
+// layer's MMAs (K = 16 each) and commits them to an mbarrier; all threads
+// wait on it, read their rows of the accumulator with tcgen05.ld, add the
+// bias, apply ReLU, and write BF16 activations back to shared memory as the
+// next layer's A operand.  After layer 4, the top 8 of each row's 64 logits
+// are packed one byte each.  Operands use the canonical K-major layout with
+// no swizzling (canon_off): the shared-memory descriptors carry the start
+// address, the 128-byte stride between core matrices along K and the stride
+// between 8-row groups.  Every wait on the mbarrier has an iteration limit;
+// a wait that runs out raises IVM_ERR_TIMEOUT, and the CTA still releases
+// its tensor memory before it returns.
+
+constexpr int kTcThreads = 512;          // two warpgroups of 8 warps, one tile in flight each
+constexpr int kTcGroup = 256;            // threads per warpgroup
+constexpr int kTcParts = 2;              // threads of a warpgroup per pair (row)
+constexpr int kTcRows = 128;             // pairs per tile (MMA M)
+constexpr size_t kTcABytes = sizeof(__nv_bfloat16) * kTcRows * kRH;        // one A buffer
+constexpr size_t kTcOffA = sizeof(__nv_bfloat16) * kRTEnd;                  // after the weights
+constexpr size_t kTcOffBar = kTcOffA + 2 * kTcABytes;
+constexpr size_t kTcSmem = kTcOffBar + 64;
+constexpr uint32_t kTcCols = 256;        // TMEM columns: 128 fp32 per warpgroup
+constexpr int kTcWaitLimit = 1 << 24;
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
 {
-    asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
-                 "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
-                 : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-                 : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+    return (uint32_t)__cvta_generic_to_shared(p);
 }
 
-__device__ __forceinline__ unsigned pack_relu(float lo, float hi)
+// Shared-memory matrix descriptor: start address, leading (along K) and
+// stride (between 8-row groups) byte offsets, descriptor version 1, no
+// swizzling, base offset 0.
+__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
 {
-    __nv_bfloat162 h = __floats2bfloat162_rn(fmaxf(lo, 0.f), fmaxf(hi, 0.f));
-    return *reinterpret_cast<unsigned *>(&h);
+    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
 }
 
-__device__ __forceinline__ unsigned lds32(const __nv_bfloat16 *p)
+// Instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both
+// K-major, N / 8 and M / 16 in their fields.
+__host__ __device__ constexpr uint32_t tc_idesc(int M, int N)
 {
-    return *reinterpret_cast<const unsigned *>(p);
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
+           ((uint32_t)(M >> 4) << 24);
 }
 
-// One hidden layer 128 -> 128 from A fragments `a` (8 k-steps); result in acc.
-__device__ __forceinline__ void layer128(const unsigned (&a)[8][4], const __nv_bfloat16 *Wt,
-                                         const float *bias, float (&acc)[16][4], int r0, int q)
+__device__ __forceinline__ void tc_mma(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                       uint32_t accumulate)
 {
-#pragma unroll
-    for (int t = 0; t < 16; t++) {
-        const float b0 = bias[8 * t + 2 * q], b1 = bias[8 * t + 2 * q + 1];
-        acc[t][0] = b0; acc[t][1] = b1; acc[t][2] = b0; acc[t][3] = b1;
-    }
-#pragma unroll
-    for (int s = 0; s < 8; s++)
-#pragma unroll
-        for (int t = 0; t < 16; t++) {
-            const __nv_bfloat16 *w = Wt + (8 * t + r0) * kRS2 + 16 * s + 2 * q;
-            mma_bf16(acc[t], a[s][0], a[s][1], a[s][2], a[s][3], lds32(w), lds32(w + 8));
-        }
+    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                 "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+                 "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
 }
 
-__device__ __forceinline__ void to_frags(const float (&acc)[16][4], unsigned (&a)[8][4])
+__device__ __forceinline__ void tc_commit(uint32_t mbar)
 {
-#pragma unroll
-    for (int s = 0; s < 8; s++) {
-        a[s][0] = pack_relu(acc[2 * s][0], acc[2 * s][1]);
-        a[s][1] = pack_relu(acc[2 * s][2], acc[2 * s][3]);
-        a[s][2] = pack_relu(acc[2 * s + 1][0], acc[2 * s + 1][1]);
-        a[s][3] = pack_relu(acc[2 * s + 1][2], acc[2 * s + 1][3]);
-    }
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
+                 : "memory");
 }
 
-constexpr int kRankWarps = 12;   // one block per SM (the weights fill most of shared memory)
-constexpr size_t kRankSmem = sizeof(__nv_bfloat16) * (kRTEnd + kRankWarps * 16 * kRS1);
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void async_proxy_fence() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
-// Warp per 16 candidate pairs: features into shared memory, four layers on
-// the tensor cores with the activations kept in registers, then the top 8
-// logits per pair (ties to the lower cluster) packed one byte each.
-__global__ void __launch_bounds__(32 * kRankWarps, 1)
-k_rank_pairs(DevScenes g, const int2 *pairs, unsigned long long npairs,
-             const unsigned long long *count_dev, const int *ctx, RankerDev r,
-             unsigned long long *ranks, const float *feat, float *logits)
+// Waits for the mbarrier phase of parity `ph`; false when the limit ran out.
+__device__ __forceinline__ bool tc_wait(uint32_t mbar, uint32_t ph)
 {
-    extern __shared__ __align__(16) unsigned char smem[];
-    __nv_bfloat16 *W = reinterpret_cast<__nv_bfloat16 *>(smem);
-    __nv_bfloat16 *F = W + kRTEnd;
-    for (int i = threadIdx.x; i < kRTEnd / 8; i += blockDim.x)
-        reinterpret_cast<uint4 *>(W)[i] = reinterpret_cast<const uint4 *>(r.wt)[i];
-    __syncthreads();
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int r0 = lane >> 2, q = lane & 3;
-    unsigned long long total = npairs;
-    if (count_dev && *count_dev < total) total = *count_dev;
-    __nv_bfloat16 *Fw = F + warp * 16 * kRS1;
-    const float *bias = r.master;
-    for (unsigned long long base = ((unsigned long long)blockIdx.x * kRankWarps + warp) * 16;
-         base < total; base += (unsigned long long)gridDim.x * kRankWarps * 16) {
-        {   // features: lane -> pair (lane & 15), half (lane >> 4) of the 80
-            const int row = lane & 15;
-            const unsigned long long p = base + row;
-            const bool ok = p < total;
-            const int f0 = (lane >> 4) * 40;
-            if (feat) {   // precomputed feature rows [n][76]
-                for (int f = f0; f < f0 + 40; f++)
-                    Fw[row * kRS1 + f] = __float2bfloat16(ok && f < kRIn ? feat[p * kRIn + f] : 0.f);
-            } else {
-                Leaf Li = {}, Lj = {};
-                int sc = 0;
-                if (ok) {
-                    const int2 pr = pairs[p];
-                    Li = load_leaf(g.leaf, pr.x);
-                    Lj = load_leaf(g.leaf, pr.y);
-                    sc = Li.scene;
-                }
-                const int *bounds = g.bounds + 6 * sc;
-                const int *cb = ctx + (size_t)kRCtx * sc + kRCBox;
-                const PairGeom G(Li, Lj);
-                for (int f = f0; f < f0 + 40; f += 2) {
-                    const float v0 = ok ? pair_feature(f, G, Li, Lj, bounds, cb) : 0.f;
-                    const float v1 = ok ? pair_feature(f + 1, G, Li, Lj, bounds, cb) : 0.f;
-                    *reinterpret_cast<__nv_bfloat162 *>(Fw + row * kRS1 + f) =
-                        __floats2bfloat162_rn(v0, v1);
-                }
-            }
-        }
-        __syncwarp();
-        float acc[16][4];
-        unsigned a[8][4];
-        // layer 1: 80 -> 128
+    uint32_t done = 0;
+    for (int it = 0; it < kTcWaitLimit && !done; it++)
+        asm volatile("{\n\t.reg .pred P1;\n\tmbarrier.try_wait.parity.shared::cta.b64 P1, [%1], %2;\n\t"
+                     "selp.b32 %0, 1, 0, P1;\n\t}"
+                     : "=r"(done)
+                     : "r"(mbar), "r"(ph));
+    return done != 0;
+}
+
+// 16 consecutive fp32 columns of this thread's TMEM lane.
+__device__ __forceinline__ void tc_ld16(uint32_t taddr, float (&v)[16])
+{
+    uint32_t r[16];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+                 "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+                   "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]),
+                   "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-        for (int t = 0; t < 16; t++) {
-            const float b0 = bias[kRB1 + 8 * t + 2 * q], b1 = bias[kRB1 + 8 * t + 2 * q + 1];
-            acc[t][0] = b0; acc[t][1] = b1; acc[t][2] = b0; acc[t][3] = b1;
-        }
+    for (int j = 0; j < 16; j++) v[j] = __uint_as_float(r[j]);
+}
+
+// One layer: K / 16 MMAs from the A buffer and weight block w (B operand,
+// N rows), into TMEM; issued by thread 0, completion on the mbarrier.
+__device__ __forceinline__ void tc_layer(uint32_t tmem, uint32_t a_addr, uint32_t w_addr, int K,
+                                         int N, uint32_t mbar)
+{
+    const uint32_t sbo = (uint32_t)(K / 8) * 128u, idesc = tc_idesc(kTcRows, N);
+    for (int ks = 0; ks < K / 16; ks++)
+        tc_mma(tmem, tc_desc(a_addr + 256u * ks, 128u, sbo), tc_desc(w_addr + 256u * ks, 128u, sbo),
+               idesc, ks > 0);
+    tc_commit(mbar);
+}
+
+// Bias and ReLU of this thread's 64 accumulator columns [c0, c0 + 64) of
+// TMEM lane `row`, written as BF16 to the A buffer (K = 128 layout).
+__device__ __forceinline__ void tc_hidden(uint32_t trow, int row, int c0, const float *bias,
+                                          __nv_bfloat16 *A)
+{
 #pragma unroll
-        for (int s = 0; s < kRInPad / 16; s++) {
-            const __nv_bfloat16 *x = Fw + r0 * kRS1 + 16 * s + 2 * q;
-            const unsigned a0 = lds32(x), a1 = lds32(x + 8 * kRS1), a2 = lds32(x + 8),
-                           a3 = lds32(x + 8 * kRS1 + 8);
-#pragma unroll
-            for (int t = 0; t < 16; t++) {
-                const __nv_bfloat16 *w = W + kRT1 + (8 * t + r0) * kRS1 + 16 * s + 2 * q;
-                mma_bf16(acc[t], a0, a1, a2, a3, lds32(w), lds32(w + 8));
-            }
-        }
-        __syncwarp();   // features of this tile are consumed
-        to_frags(acc, a);
-        layer128(a, W + kRT2, bias + kRB2, acc, r0, q);
-        to_frags(acc, a);
-        layer128(a, W + kRT3, bias + kRB3, acc, r0, q);
-        to_frags(acc, a);
-        // layer 4: 128 -> 64
-        float z[8][4];
-#pragma unroll
-        for (int t = 0; t < 8; t++) {
-            const float b0 = bias[kRB4 + 8 * t + 2 * q], b1 = bias[kRB4 + 8 * t + 2 * q + 1];
-            z[t][0] = b0; z[t][1] = b1; z[t][2] = b0; z[t][3] = b1;
-        }
-#pragma unroll
-        for (int s = 0; s < 8; s++)
-#pragma unroll
-            for (int t = 0; t < 8; t++) {
-                const __nv_bfloat16 *w = W + kRT4 + (8 * t + r0) * kRS2 + 16 * s + 2 * q;
-                mma_bf16(z[t], a[s][0], a[s][1], a[s][2], a[s][3], lds32(w), lds32(w + 8));
-            }
-        if (logits) {
-#pragma unroll
-            for (int h = 0; h < 2; h++) {
-                const unsigned long long p = base + r0 + 8 * h;
-                if (p < total)
-#pragma unroll
-                    for (int t = 0; t < 8; t++) {
-                        logits[p * kROut + 8 * t + 2 * q] = z[t][2 * h];
-                        logits[p * kROut + 8 * t + 2 * q + 1] = z[t][2 * h + 1];
-                    }
-            }
-        }
-        // top 8 of the 64 logits of rows r0 and r0 + 8 (a quad of lanes holds a row)
+    for (int c = 0; c < 64; c += 16) {
+        float v[16];
+        tc_ld16(trow + (uint32_t)(c0 + c), v);
 #pragma unroll
         for (int h = 0; h < 2; h++) {
-            unsigned long long packed = 0;
-            float v[16];
+            __align__(16) __nv_bfloat162 q[4];
 #pragma unroll
-            for (int t = 0; t < 8; t++) {
-                v[2 * t] = z[t][2 * h];
-                v[2 * t + 1] = z[t][2 * h + 1];
+            for (int j = 0; j < 4; j++) {
+                const int k = 8 * h + 2 * j;
+                q[j] = __floats2bfloat162_rn(fmaxf(v[k] + __ldg(bias + c0 + c + k), 0.f),
+                                             fmaxf(v[k + 1] + __ldg(bias + c0 + c + k + 1), 0.f));
             }
+            *reinterpret_cast<uint4 *>(A + canon_off(row, c0 + c + 8 * h, kRH)) =
+                *reinterpret_cast<const uint4 *>(q);
+        }
+    }
+}
+
+// Barrier of one warpgroup (named barrier 1 + group, 256 threads).
+__device__ __forceinline__ void group_sync(int group)
+{
+    asm volatile("bar.sync %0, %1;" ::"r"(1 + group), "r"(kTcGroup) : "memory");
+}
+
+// The k best of a thread's 32 logits, best first (ties to the lower column).
+__device__ __forceinline__ void top_of32(const float (&z)[32], int c0, float (&bv)[kRTop],
+                                         int (&bc)[kRTop])
+{
+    unsigned taken = 0;
+#pragma unroll
+    for (int k = 0; k < kRTop; k++) {
+        float v = -INFINITY;
+        int c = 255;
+#pragma unroll
+        for (int j = 0; j < 32; j++) {
+            const bool free = !((taken >> j) & 1u);
+            if (free && (z[j] > v || (z[j] == v && c0 + j < c))) { v = z[j]; c = c0 + j; }
+        }
+        if (c < 255) taken |= 1u << (c - c0);
+        bv[k] = v;
+        bc[k] = c;
+    }
+}
+
+// Tiles of 128 candidate pairs (or precomputed feature rows when `feat` is
+// given): 76 features, four layers on the tensor cores, then the top 8 of
+// the 64 logits per pair (ties to the lower cluster) packed one byte each.
+// The two warpgroups take alternate tiles, each with its own A buffer, TMEM
+// columns and mbarrier, so that one group's MMAs run while the other works.
+__global__ void __launch_bounds__(kTcThreads, 1)
+k_rank_pairs(DevScenes g, const int2 *pairs, unsigned long long npairs,
+             const unsigned long long *count_dev, const int *ctx, RankerDev r,
+             unsigned long long *ranks, const float *feat, float *logits, int *err)
+{
+    extern __shared__ __align__(1024) unsigned char smem[];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int group = tid / kTcGroup, gtid = tid % kTcGroup, gwarp = warp & 7;
+    __nv_bfloat16 *W = reinterpret_cast<__nv_bfloat16 *>(smem);
+    __nv_bfloat16 *A = reinterpret_cast<__nv_bfloat16 *>(smem + kTcOffA + group * kTcABytes);
+    unsigned long long *bar = reinterpret_cast<unsigned long long *>(smem + kTcOffBar);
+    uint32_t *slot = reinterpret_cast<uint32_t *>(smem + kTcOffBar + 16);
+    int *stop = reinterpret_cast<int *>(smem + kTcOffBar + 24);   // [2] per group
+    // after layer 4 a group's A buffer holds each row's candidates: [row][part][k]
+    float *cv = reinterpret_cast<float *>(A);
+    int *ci = reinterpret_cast<int *>(A) + kTcRows * kTcParts * kRTop;
+    for (int i = tid; i < kRTEnd / 8; i += kTcThreads)
+        reinterpret_cast<uint4 *>(W)[i] = __ldg(reinterpret_cast<const uint4 *>(r.wt) + i);
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar + 1)));
+        stop[0] = stop[1] = 0;
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(slot)),
+                     "r"(kTcCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    async_proxy_fence();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *slot + 128u * group;
+    const uint32_t mbar = smem_u32(bar + group), a_addr = smem_u32(A), w_addr = smem_u32(W);
+    unsigned long long total = npairs;
+    if (count_dev && *count_dev < total) total = *count_dev;
+    const unsigned long long ntiles = (total + kTcRows - 1) / kTcRows;
+    // features: thread -> (row, half of the 80 columns); accumulator: warp
+    // w reads TMEM lanes 32 (w % 4) .. + 31, two warps of the group per lane
+    // quarter, each with half of the columns
+    const int row = gtid & (kTcRows - 1), part = gtid >> 7;
+    const int arow = 32 * (gwarp & 3) + lane, apart = gwarp >> 2;
+    const uint32_t trow = tmem + ((uint32_t)(32 * (gwarp & 3)) << 16);
+    const float *bias = r.master;
+    const int k0 = 40 * part;
+    uint32_t ph = 0;
+    for (unsigned long long tile = 2ull * blockIdx.x + group; tile < ntiles;
+         tile += 2ull * gridDim.x) {
+        const unsigned long long base = tile * kTcRows;
+        {
+            const unsigned long long p = base + row;
+            const bool in = p < total;
+            Leaf Li = {}, Lj = {};
+            int sc = 0;
+            if (in && !feat) {
+                const int2 pr = pairs[p];
+                Li = load_leaf(g.leaf, pr.x);
+                Lj = load_leaf(g.leaf, pr.y);
+                sc = Li.scene;
+            }
+            const int *bounds = feat ? nullptr : g.bounds + 6 * sc;
+            const int *cb = feat ? nullptr : ctx + (size_t)kRCtx * sc;
+            const PairGeom G(Li, Lj);
+            for (int c = k0; c < k0 + 40; c += 8) {
+                float v[8];
+#pragma unroll
+                for (int j = 0; j < 8; j++) {
+                    const int f = c + j;
+                    v[j] = !in || f >= kRIn ? 0.f
+                         : (feat ? __ldg(feat + p * kRIn + f) : pair_feature(f, G, Li, Lj, bounds, cb));
+                }
+                __align__(16) __nv_bfloat162 q[4];
+#pragma unroll
+                for (int j = 0; j < 4; j++) q[j] = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+                *reinterpret_cast<uint4 *>(A + canon_off(row, c, kRK1)) =
+                    *reinterpret_cast<const uint4 *>(q);
+            }
+        }
+        async_proxy_fence();
+        tc_fence_before();
+        group_sync(group);
+        bool ok = true;
+        // layers 1-4: 80 -> 128, 128 -> 128, 128 -> 128 (ReLU), 128 -> 64
+#pragma unroll
+        for (int l = 0; l < 4; l++) {
+            const int K = l == 0 ? kRK1 : kRH, N = l == 3 ? kROut : kRH;
+            const int wbase = l == 0 ? kRT1 : (l == 1 ? kRT2 : (l == 2 ? kRT3 : kRT4));
+            if (gtid == 0) {
+                tc_fence_after();
+                tc_layer(tmem, a_addr, w_addr + 2u * wbase, K, N, mbar);
+            }
+            if (!tc_wait(mbar, ph)) stop[group] = 1;
+            ph ^= 1u;
+            group_sync(group);
+            if (stop[group]) { ok = false; break; }
+            tc_fence_after();
+            if (l < 3) {
+                const int bbase = l == 0 ? kRB1 : (l == 1 ? kRB2 : kRB3);
+                tc_hidden(trow, arow, 64 * apart, bias + bbase, A);
+                async_proxy_fence();
+                tc_fence_before();
+                group_sync(group);
+            }
+        }
+        if (!ok) break;
+        {   // each thread: 32 of its row's logits, their best 8 as candidates
+            const int c0 = 32 * apart;
+            float z[32];
+            {
+                float v[16];
+                tc_ld16(trow + (uint32_t)c0, v);
+#pragma unroll
+                for (int j = 0; j < 16; j++) z[j] = v[j];
+                tc_ld16(trow + (uint32_t)(c0 + 16), v);
+#pragma unroll
+                for (int j = 0; j < 16; j++) z[16 + j] = v[j];
+            }
+#pragma unroll
+            for (int j = 0; j < 32; j++) z[j] += __ldg(bias + kRB4 + c0 + j);
+            const unsigned long long p = base + arow;
+            if (logits && p < total) {
+#pragma unroll
+                for (int j = 0; j < 32; j++) logits[p * kROut + c0 + j] = z[j];
+            }
+            float bv[kRTop];
+            int bc[kRTop];
+            top_of32(z, c0, bv, bc);
+            const int o = (arow * kTcParts + apart) * kRTop;
+#pragma unroll
+            for (int k = 0; k < kRTop; k++) { cv[o + k] = bv[k]; ci[o + k] = bc[k]; }
+        }
+        tc_fence_before();
+        group_sync(group);
+        if (gtid < kTcRows) {   // merge the two sorted candidate lists of row `gtid`
+            const unsigned long long p = base + gtid;
+            int ha = 0, hb = 0;
+            unsigned long long packed = 0;
+            const int o = gtid * kTcParts * kRTop;
 #pragma unroll
             for (int k = 0; k < kRTop; k++) {
-                float bv = -INFINITY;
-                int bc = 255;
-#pragma unroll
-                for (int i = 0; i < 16; i++) {
-                    const int col = 8 * (i >> 1) + 2 * q + (i & 1);
-                    if (v[i] > bv || (v[i] == bv && col < bc)) { bv = v[i]; bc = col; }
-                }
-#pragma unroll
-                for (int off = 1; off <= 2; off <<= 1) {
-                    const float ov = __shfl_xor_sync(kFull, bv, off);
-                    const int oc = __shfl_xor_sync(kFull, bc, off);
-                    if (ov > bv || (ov == bv && oc < bc)) { bv = ov; bc = oc; }
-                }
-#pragma unroll
-                for (int i = 0; i < 16; i++)
-                    if (8 * (i >> 1) + 2 * q + (i & 1) == bc) v[i] = -INFINITY;
-                packed |= (unsigned long long)(bc & 0xff) << (8 * k);
+                // a list holds 8 and 8 are taken in all, so a head past its
+                // list is never compared
+                const float va = ha < kRTop ? cv[o + ha] : -INFINITY;
+                const int ca = ha < kRTop ? ci[o + ha] : 256;
+                const float vb = hb < kRTop ? cv[o + kRTop + hb] : -INFINITY;
+                const int cb2 = hb < kRTop ? ci[o + kRTop + hb] : 256;
+                const bool take_a = va > vb || (va == vb && ca < cb2);
+                packed |= (unsigned long long)((take_a ? ca : cb2) & 0xff) << (8 * k);
+                ha += take_a;
+                hb += !take_a;
             }
-            const unsigned long long p = base + r0 + 8 * h;
-            if (q == 0 && p < total) ranks[p] = packed;
+            if (p < total) ranks[p] = packed;
         }
+        group_sync(group);   // the accumulator and the A buffer are free for the next tile
+    }
+    if (gtid == 0 && stop[group]) raise_error(err, IVM_ERR_TIMEOUT);
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(*slot),
+                     "r"(kTcCols));
     }
 }
 
 cudaError_t ranker_rank_pairs(const DevScenes &g, const int2 *pairs, unsigned long long npairs,
                               const unsigned long long *count_dev, const int *ctx,
-                              const RankerDev &r, unsigned long long *ranks, int n_sm,
+                              const RankerDev &r, unsigned long long *ranks, int n_sm, int *err,
                               cudaStream_t st)
 {
     if (npairs == 0) return cudaSuccess;
-    cudaFuncSetAttribute(k_rank_pairs, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)kRankSmem);
-    const unsigned long long tiles = (npairs + 15) / 16;
-    unsigned long long blocks = (tiles + kRankWarps - 1) / kRankWarps;
-    if (blocks > (unsigned long long)n_sm) blocks = (unsigned long long)n_sm;
-    k_rank_pairs<<<(unsigned)blocks, 32 * kRankWarps, kRankSmem, st>>>(
-        g, pairs, npairs, count_dev, ctx, r, ranks, nullptr, nullptr);
+    cudaError_t e = cudaFuncSetAttribute(k_rank_pairs, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kTcSmem);
+    if (e != cudaSuccess) return e;
+    const unsigned long long tiles = (npairs + 2 * kTcRows - 1) / (2 * kTcRows);   // tile pairs
+    const unsigned blocks = (unsigned)(tiles < (unsigned long long)n_sm ? tiles : n_sm);
+    k_rank_pairs<<<blocks, kTcThreads, kTcSmem, st>>>(g, pairs, npairs, count_dev, ctx, r, ranks,
+                                                      nullptr, nullptr, err);
     note_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t ranker_infer(const float *feat, unsigned long long n, const RankerDev &r,
-                         float *logits, unsigned long long *ranks, int n_sm, cudaStream_t st)
+                         float *logits, unsigned long long *ranks, int n_sm, int *err,
+                         cudaStream_t st)
 {
     if (n == 0) return cudaSuccess;
-    cudaFuncSetAttribute(k_rank_pairs, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)kRankSmem);
-    const unsigned long long tiles = (n + 15) / 16;
-    unsigned long long blocks = (tiles + kRankWarps - 1) / kRankWarps;
-    if (blocks > (unsigned long long)n_sm) blocks = (unsigned long long)n_sm;
-    k_rank_pairs<<<(unsigned)blocks, 32 * kRankWarps, kRankSmem, st>>>(
-        DevScenes{}, nullptr, n, nullptr, nullptr, r, ranks, feat, logits);
+    cudaError_t e = cudaFuncSetAttribute(k_rank_pairs, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kTcSmem);
+    if (e != cudaSuccess) return e;
+    const unsigned long long tiles = (n + 2 * kTcRows - 1) / (2 * kTcRows);   // tile pairs
+    const unsigned blocks = (unsigned)(tiles < (unsigned long long)n_sm ? tiles : n_sm);
+    k_rank_pairs<<<blocks, kTcThreads, kTcSmem, st>>>(DevScenes{}, nullptr, n, nullptr, nullptr, r,
+                                                      ranks, feat, logits, err);
     note_launches(1);
     return cudaGetLastError();
 }
@@ -410,7 +558,7 @@ __global__ void k_log_hits(DevScenes g, const int2 *pairs, unsigned long long np
     const int *C = ctx + (size_t)kRCtx * Li.scene;
     const PairGeom G(Li, Lj);
     for (int f = lane; f < kRInPad; f += 32)
-        feat[w * kRInPad + f] = pair_feature(f, G, Li, Lj, g.bounds + 6 * Li.scene, C + kRCBox);
+        feat[w * kRInPad + f] = pair_feature(f, G, Li, Lj, g.bounds + 6 * Li.scene, C);
     const bool facing = front_of(Lj, px, py, pz) && front_of(Li, qx, qy, qz);
     float best_t = 2.f;
     int best_pos = -1;
@@ -442,25 +590,31 @@ cudaError_t ranker_log_hits(const DevScenes &g, const int2 *pairs, unsigned long
 
 // ------------------------------------------------------------ weights
 
+// Thread per (n, k) of the four W^T blocks in natural order; writes the BF16
+// value to its place in the canonical layout (zero in layer 1's padding).
 __global__ void k_pack(const float *m, __nv_bfloat16 *wt)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= kRTEnd) return;
+    int base, K, n, k;
     float v = 0.f;
-    if (i < kRT2) {                        // W1^T [128][88]
-        const int n = i / kRS1, k = i % kRS1;
+    if (i < kRT2) {                        // W1^T [128][80]
+        base = kRT1; K = kRK1; n = i / kRK1; k = i % kRK1;
         if (k < kRIn) v = m[kRW1 + k * kRH + n];
-    } else if (i < kRT3) {
-        const int j = i - kRT2, n = j / kRS2, k = j % kRS2;
-        if (k < kRH) v = m[kRW2 + k * kRH + n];
-    } else if (i < kRT4) {
-        const int j = i - kRT3, n = j / kRS2, k = j % kRS2;
-        if (k < kRH) v = m[kRW3 + k * kRH + n];
-    } else {
-        const int j = i - kRT4, n = j / kRS2, k = j % kRS2;
-        if (k < kRH) v = m[kRW4 + k * kROut + n];
+    } else if (i < kRT3) {                 // W2^T [128][128]
+        const int j = i - kRT2;
+        base = kRT2; K = kRH; n = j / kRH; k = j % kRH;
+        v = m[kRW2 + k * kRH + n];
+    } else if (i < kRT4) {                 // W3^T [128][128]
+        const int j = i - kRT3;
+        base = kRT3; K = kRH; n = j / kRH; k = j % kRH;
+        v = m[kRW3 + k * kRH + n];
+    } else {                               // W4^T [64][128]
+        const int j = i - kRT4;
+        base = kRT4; K = kRH; n = j / kRH; k = j % kRH;
+        v = m[kRW4 + k * kROut + n];
     }
-    wt[i] = __float2bfloat16(v);
+    wt[base + canon_off(n, k, K)] = __float2bfloat16(v);
 }
 
 cudaError_t ranker_pack(const float *master, __nv_bfloat16 *wt, cudaStream_t st)

@@ -16,9 +16,9 @@
 // pair's two facet centroids normalised to the scene box (6), both unit
 // normals (6), and per cluster the entry depth of the centroid-to-centroid
 // segment into the cluster's box (1 - t_entry if it meets the box, else 0;
-// 64).  Inference runs BF16 weights with FP32 accumulation on the tensor
-// cores (warp-level mma m16n8k16, 16 pairs per warp); training keeps FP32
-// master weights.
+// 64).  Inference runs BF16 weights with FP32 accumulation on the 5th-generation
+// tensor cores (tcgen05.mma, 128 pairs per tile, operands in shared memory,
+// accumulators in tensor memory); training keeps FP32 master weights.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -37,11 +37,21 @@ constexpr int kRW3 = kRB2 + kRH, kRB3 = kRW3 + kRH * kRH;
 constexpr int kRW4 = kRB3 + kRH, kRB4 = kRW4 + kRH * kROut;
 constexpr int kRParams = kRB4 + kROut;   // 51,136
 
-// BF16 inference copy: transposed W^T[out][in] with padded rows (conflict-free
-// fragment loads), FP32 biases.
-constexpr int kRS1 = 88, kRS2 = 136;   // row strides in bf16 elements
-constexpr int kRT1 = 0, kRT2 = kRT1 + kRH * kRS1, kRT3 = kRT2 + kRH * kRS2,
-              kRT4 = kRT3 + kRH * kRS2, kRTEnd = kRT4 + kROut * kRS2;   // bf16 elements
+// BF16 inference copy for the tensor cores: each layer's W^T[out][in] (the
+// B operand, N = out rows, K = in columns) in the canonical K-major layout of
+// tcgen05.mma without swizzling: 8 x 8 core matrices of 128 contiguous bytes
+// (8 rows of 16 bytes), core matrices along K 128 bytes apart, 8-row groups
+// K / 8 core matrices apart.  Layer 1's K is the 76 inputs padded to 80.
+// FP32 biases are read from the master weights.
+constexpr int kRK1 = 80;
+constexpr int kRT1 = 0, kRT2 = kRT1 + kRH * kRK1, kRT3 = kRT2 + kRH * kRH,
+              kRT4 = kRT3 + kRH * kRH, kRTEnd = kRT4 + kROut * kRH;   // bf16 elements
+
+// Element offset of (row, k) in a canonical K-major operand with K columns.
+__host__ __device__ constexpr int canon_off(int row, int k, int K)
+{
+    return (row >> 3) * (K >> 3) * 64 + (k >> 3) * 64 + (row & 7) * 8 + (k & 7);
+}
 
 struct RankerDev {
     const __nv_bfloat16 *wt;   // kRTEnd elements
@@ -52,9 +62,13 @@ struct RankerDev {
 // clusters lo > hi), the 64 cut nodes (node index, or ~facet for a leaf) and
 // 65 sorted-range starts (cluster c = positions [start[c], start[c + 1]);
 // unused clusters are empty ranges at n).
+// The boxes are also kept as floats of twice their value (the features work
+// in 2x scaled units; exact below 2^23), so that the features need no
+// integer conversions.
 constexpr int kRCBox = 0, kRCut = 6 * kRClusters, kRCStart = kRCut + kRClusters;
-constexpr int kRCtx = 516;   // >= kRCStart + kRClusters + 1, a multiple of 4
-static_assert(kRCStart + kRClusters + 1 <= kRCtx, "cluster context");
+constexpr int kRCFBox = 516;   // >= kRCStart + kRClusters + 1, a multiple of 4
+constexpr int kRCtx = kRCFBox + 6 * kRClusters;
+static_assert(kRCStart + kRClusters + 1 <= kRCFBox, "cluster context");
 
 // Cluster holding sorted position pos (starts ascending, start[0] = 0).
 __device__ __forceinline__ int cluster_at(const int *start, int pos)
@@ -98,9 +112,9 @@ struct PairGeom {
 };
 
 // Feature f (0..79) of the pair (Li, Lj); bounds are the scene's centroid
-// bounds (lo + hi units), cbox the scene's 64 cluster boxes (int, lo xyz hi xyz).
+// bounds (lo + hi units), C the scene's cluster context (its float boxes).
 __device__ __forceinline__ float pair_feature(int f, const PairGeom &G, const Leaf &Li,
-                                              const Leaf &Lj, const int *bounds, const int *cbox)
+                                              const Leaf &Lj, const int *bounds, const int *C)
 {
     if (f < 6) {   // centroids, normalised to the scene's centroid box
         const int a = f % 3;
@@ -118,14 +132,14 @@ __device__ __forceinline__ float pair_feature(int f, const PairGeom &G, const Le
     }
     if (f >= kRIn) return 0.f;
     // entry depth of the centroid segment into cluster box c: 1 - t_entry
-    const int *b = cbox + 6 * (f - 12);
-    const int b0 = __ldg(b), b3 = __ldg(b + 3);
+    const float *b = reinterpret_cast<const float *>(C + kRCFBox) + 6 * (f - 12);
+    const float b0 = __ldg(b), b3 = __ldg(b + 3);
     if (b0 > b3) return 0.f;   // empty cluster
     float tn = 0.f, tf = 1.f;
 #pragma unroll
     for (int a = 0; a < 3; a++) {
-        const float lo = 2.f * (a == 0 ? b0 : __ldg(b + a));
-        const float hi = 2.f * (a == 0 ? b3 : __ldg(b + 3 + a));
+        const float lo = a == 0 ? b0 : __ldg(b + a);
+        const float hi = a == 0 ? b3 : __ldg(b + 3 + a);
         if (G.d[a] == 0.f) {
             if (G.p[a] < lo || G.p[a] > hi) return 0.f;
             continue;
@@ -141,14 +155,18 @@ __device__ __forceinline__ float pair_feature(int f, const PairGeom &G, const Le
 // The cut, cluster boxes and starts of every scene into ctx [n_scenes][kRCtx],
 // and ncl [total_nodes] (after the BVH is built).
 cudaError_t ranker_clusters(const DevScenes &g, int *ctx, signed char *ncl, cudaStream_t st);
+// Top-8 clusters of every candidate pair (tensor cores; one CTA per SM, 135 KB
+// of shared memory and 128 TMEM columns each); IVM_ERR_TIMEOUT into err if a
+// wait for the tensor cores runs out.
 cudaError_t ranker_rank_pairs(const DevScenes &g, const int2 *pairs, unsigned long long npairs,
                               const unsigned long long *count_dev, const int *ctx,
-                              const RankerDev &r, unsigned long long *ranks, int n_sm,
+                              const RankerDev &r, unsigned long long *ranks, int n_sm, int *err,
                               cudaStream_t st);
 // The same network over precomputed feature rows [n][76]: logits [n][64]
 // and packed top-8 cluster indices [n].
 cudaError_t ranker_infer(const float *feat, unsigned long long n, const RankerDev &r,
-                         float *logits, unsigned long long *ranks, int n_sm, cudaStream_t st);
+                         float *logits, unsigned long long *ranks, int n_sm, int *err,
+                         cudaStream_t st);
 cudaError_t ranker_log_hits(const DevScenes &g, const int2 *pairs, unsigned long long npairs,
                             const int *ctx, float *feat, int *label,
                             unsigned long long *cursor, unsigned long long cap, int *err,

@@ -81,11 +81,15 @@ def test_gradients_reject_bad_labels(ctx):
         ivm.ivm_ranker_gradients(ctx, w, x, np.array([0, 64], np.int32))
 
 
-def test_inference_kernel_matches_float64_reference(fresh_ctx):
+@pytest.mark.parametrize("rows", [1000, 40_000])
+def test_inference_kernel_matches_float64_reference(fresh_ctx, rows):
+    """The tensor-core kernel (tcgen05, 128 rows per tile, one CTA per SM):
+    1000 rows = 7 tiles + 104 (a ragged last tile); 40,000 rows = 313 tiles,
+    so each CTA takes two or three tiles in turn."""
     rng = np.random.default_rng(7)
     w = he_weights(rng)
     ivm.ivm_ranker_load(fresh_ctx, blob_of(w))
-    x = rng.random((1000, 76)).astype(np.float32)     # ragged: 1000 = 62 tiles of 16 + 8
+    x = rng.random((rows, 76)).astype(np.float32)
     logits, top = ivm.ivm_ranker_infer(fresh_ctx, x)
     # float64 forward of the same weights
     h = x.astype(np.float64)

@@ -785,6 +785,9 @@ def run_ours(args, ws, rank, local):
             "matrix_leaf_tests_per_segment_without_ranker":
                 per_seg(tf["stats"]["matrix"], "leaf_tests"),
             "first_proposal_hits": tl["stats"]["matrix"]["ranker_hits"],
+            "hits_at_8": tl["stats"]["matrix"]["ranker_hits8"],
+            "hits_note": "segments blocked inside the first proposed cluster / inside any of "
+                         "the up to 8 proposals walked first, of the matrix call's segments",
             "train": {"scenes": "tiny (41 facets) + degenerate district (1,001 facets)",
                       "epochs": 12, "final_loss": train_loss, "seconds": train_s}},
         "forms_bit_identical": agree,

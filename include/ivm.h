@@ -120,6 +120,9 @@ typedef struct ivm_stats {
     uint64_t cache_hits;      /* segments blocked by an occluder-cache facet */
     uint64_t dedup_rows;      /* table rows copied from an equal-position row */
     float ms_ingest, ms_bvh, ms_screen, ms_traverse, ms_tree, ms_total;
+    uint64_t ranker_hits8;    /* blocked segments whose occluder lay in one of the
+                                 ranker's proposed clusters walked first (LEARNED;
+                                 up to 8 per pair: hits at 8) */
 } ivm_stats;
 
 typedef struct ivm_tree_summary {

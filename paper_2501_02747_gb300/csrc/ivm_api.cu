@@ -317,6 +317,7 @@ int fill_stats(ivm_ctx *c, ivm_stats *st, unsigned long long pairs, int phases)
     st->undecided = c->h_ctr[C_UNDECIDED];
     st->exact_tests = c->h_ctr[C_EXACT_TESTS];
     st->ranker_hits = c->h_ctr[C_RANKER_HITS];
+    st->ranker_hits8 = c->h_ctr[C_RANKER_HITS8];
     st->cache_hits = c->h_ctr[C_CACHE_HITS];
     st->dedup_rows = c->h_ctr[C_DEDUP_ROWS];
     st->ms_ingest = elapsed(c->ev[0], c->ev[1]);

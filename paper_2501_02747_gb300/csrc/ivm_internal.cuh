@@ -76,6 +76,7 @@ enum Counter {
     C_CAND_PAIRS,
     C_CACHE_HITS,
     C_DEDUP_ROWS,
+    C_RANKER_HITS8,
     C_COUNT_
 };
 

@@ -53,6 +53,7 @@ __device__ __forceinline__ unsigned occlude_ranked(Seg &s, unsigned alive, const
         done |= 1ull << c;
         if (blocker >= 0) last = blocker;
         if (k == 0) wc.ranker_hits += ((before & ~alive) >> lane) & 1u;
+        wc.ranker_hits8 += ((before & ~alive) >> lane) & 1u;
         if (!alive) {
             if (CACHE) cache.put(last);
             return 0;

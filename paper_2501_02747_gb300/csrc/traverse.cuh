@@ -232,7 +232,7 @@ __device__ __forceinline__ Leaf load_leaf(const Leaf *leaves, int g)
 // A lane does far fewer than 2^32 tests in one launch.
 struct WalkCounters {
     unsigned node_tests = 0, leaf_tests = 0, undecided = 0, exact = 0, segments = 0,
-             cache_hits = 0, ranker_hits = 0;
+             cache_hits = 0, ranker_hits = 0, ranker_hits8 = 0;
 };
 
 // Traversal kernels run 128-thread blocks; the minimum-blocks hint caps
@@ -254,10 +254,11 @@ __device__ __forceinline__ void flush_counters(const WalkCounters &wc, unsigned 
     unsigned long long a = warp_sum(wc.node_tests), b = warp_sum(wc.leaf_tests),
                        c = warp_sum(wc.undecided), d = warp_sum(wc.exact),
                        e = warp_sum(wc.segments), f = warp_sum(wc.cache_hits),
-                       h = warp_sum(wc.ranker_hits);
+                       h = warp_sum(wc.ranker_hits), h8 = warp_sum(wc.ranker_hits8);
     if ((threadIdx.x & 31) == 0) {
         if (f) atomicAdd(ctr + C_CACHE_HITS, f);
         if (h) atomicAdd(ctr + C_RANKER_HITS, h);
+        if (h8) atomicAdd(ctr + C_RANKER_HITS8, h8);
         if (a) atomicAdd(ctr + C_NODE_TESTS, a);
         if (b) atomicAdd(ctr + C_LEAF_TESTS, b);
         if (c) atomicAdd(ctr + C_UNDECIDED, c);

@@ -47,7 +47,8 @@ class ivm_stats(ctypes.Structure):
                 ("cache_hits", ctypes.c_uint64), ("dedup_rows", ctypes.c_uint64),
                 ("ms_ingest", ctypes.c_float), ("ms_bvh", ctypes.c_float),
                 ("ms_screen", ctypes.c_float), ("ms_traverse", ctypes.c_float),
-                ("ms_tree", ctypes.c_float), ("ms_total", ctypes.c_float)]
+                ("ms_tree", ctypes.c_float), ("ms_total", ctypes.c_float),
+                ("ranker_hits8", ctypes.c_uint64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -54,7 +54,7 @@ def test_struct_layouts_match_header():
     assert ctypes.sizeof(ivm.ivm_facet) == 40
     assert ctypes.sizeof(ivm.ivm_params) == 28
     assert ctypes.sizeof(ivm.ivm_tree_summary) == 24
-    assert ctypes.sizeof(ivm.ivm_stats) == 10 * 8 + 6 * 4
+    assert ctypes.sizeof(ivm.ivm_stats) == 10 * 8 + 6 * 4 + 8
     assert ctypes.sizeof(ivm.ivm_range) == 32 == ivm.RANGE_DTYPE.itemsize
     assert ctypes.sizeof(ivm.ivm_range_summary) == 32
 

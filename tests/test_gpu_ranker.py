@@ -223,6 +223,7 @@ def test_trained_ranker_cuts_the_walks(trained, fresh_ctx):
                (("plain walk", sf), ("trained", sl), ("random", sr))}
     print("\nnode tests per segment:", {k: round(v, 3) for k, v in per_seg.items()},
           f"first-proposal hits: trained {sl.ranker_hits}, random {sr.ranker_hits}")
+    assert sl.ranker_hits8 >= sl.ranker_hits and sf.ranker_hits8 == 0   # hits at 8 >= at 1
     assert per_seg["trained"] <= 0.95 * per_seg["plain walk"]
     assert per_seg["trained"] < per_seg["random"]
     assert sl.ranker_hits > sr.ranker_hits

@@ -183,7 +183,7 @@ constexpr size_t kTcOffA = sizeof(__nv_bfloat16) * kRTEnd;                  // a
 constexpr size_t kTcOffBar = kTcOffA + 2 * kTcABytes;
 constexpr size_t kTcSmem = kTcOffBar + 64;
 constexpr uint32_t kTcCols = 256;        // TMEM columns: 128 fp32 per warpgroup
-constexpr int kTcWaitLimit = 1 << 24;
+constexpr int kTcWaitLimit = 1 << 20;   // try_wait rounds before IVM_ERR_TIMEOUT
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
 {

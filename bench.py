@@ -78,8 +78,8 @@ def parse():
     p.add_argument("--rows", type=int, default=None,
                    help="profiling: decide only the pairs of the first ROWS matrix rows")
     p.add_argument("--shape", default=None,
-                   help="profiling: launch shape tile,warps_per_block,table_tile instead of "
-                        "the autotuner's")
+                   help="profiling: launch shape tile,warps_per_block,table_tile[,proof_tile] "
+                        "instead of the autotuner's")
     return p.parse_args()
 
 
@@ -308,7 +308,8 @@ class Path:
                       "learned": dict(mode=ivm.IVM_MODE_LEARNED, flags=fast)}
         self.tuned = tuned
         sm = {"tile": tuned["tile"], "warps_per_block": tuned["warps_per_block"]}
-        stt = {"tile": tuned["table_tile"], "warps_per_block": tuned["warps_per_block"]}
+        stt = {"tile": tuned["table_tile"], "warps_per_block": tuned["warps_per_block"],
+               "proof_tile": tuned.get("proof_tile", 0)}
         self.shape = {"plain": ({}, {}), "fast": (sm, stt), "fast_edge_filter": (sm, stt),
                       "learned": (sm, stt)}
         # rows the table actually traces: one per run of equal positions per side
@@ -449,8 +450,9 @@ def profile_case(args, ivm, shard, sg, ctx, dev, stream):
     tx = torch.from_numpy(sc.tx).to(dev)
     rx = torch.from_numpy(sc.rx).to(dev)
     if args.shape:
-        t, w, tt = (int(x) for x in args.shape.split(","))
-        tuned = {"tile": t, "warps_per_block": w, "table_tile": tt}
+        v = [int(x) for x in args.shape.split(",")]
+        tuned = {"tile": v[0], "warps_per_block": v[1], "table_tile": v[2],
+                 "proof_tile": v[3] if len(v) > 3 else 0}
     else:
         tuned = ivm.ivm_autotune(ctx, fd, sc.samples_per_side, tx, rx,
                                  mode=ivm.IVM_MODE_FILTERED, flags=fast_flags(ivm))
@@ -650,7 +652,8 @@ def batch_block(args, ivm, sg, ctx, dev, stream, flush):
     forms = {"fast": (dict(mode=ivm.IVM_MODE_FILTERED, flags=fast,
                            tile=tuned["tile"], warps_per_block=tuned["warps_per_block"]),
                       dict(mode=ivm.IVM_MODE_FILTERED, flags=fast,
-                           tile=tuned["table_tile"], warps_per_block=tuned["warps_per_block"])),
+                           tile=tuned["table_tile"], warps_per_block=tuned["warps_per_block"],
+                           proof_tile=tuned["proof_tile"])),
              "plain": (dict(mode=ivm.IVM_MODE_EXACT), dict(mode=ivm.IVM_MODE_EXACT))}
     res, outs = {}, {}
     for form, steps, warm in (("fast", min(args.steps, 3), 1), ("plain", 1, 0)):

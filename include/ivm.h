@@ -105,6 +105,8 @@ typedef struct ivm_params {
     int32_t warps_per_block;  /* 1..4 (0 = default 4) */
     int32_t flags;            /* IVM_FLAG_* */
     int32_t table_tile;       /* table: consecutive snapshots per work item (0 = 32) */
+    int32_t proof_tile;       /* table: snapshots per straight-stretch proof, 1..65536
+                                 (0 = 32); a launch-shape choice, same bits */
 } ivm_params;
 
 typedef struct ivm_stats {
@@ -383,8 +385,8 @@ int ivm_ranker_gradients(ivm_ctx *ctx, const float *weights, const float *x, con
  * schedule choice).  Times candidate launch shapes on a sample of the given
  * workload -- the first 8 scenes at most and the first 16,384 snapshots of
  * each -- with params' samples_per_side, mode and flags (graph replay is
- * switched off while timing), and writes the fastest warps_per_block, tile
- * and table_tile into *params.  Inputs as for ivm_build_table (host or
+ * switched off while timing), and writes the fastest warps_per_block, tile,
+ * table_tile and proof_tile into *params.  Inputs as for ivm_build_table (host or
  * device; tx, rx, n_snap may be NULL to tune the matrix only).  The outputs
  * of the trial runs go to the context's scratch.  Errors: as
  * ivm_build_table. */

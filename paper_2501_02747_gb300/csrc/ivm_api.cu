@@ -156,6 +156,7 @@ int check_params(const ivm_params *p)
     if (p->mode < IVM_MODE_EXACT || p->mode > IVM_MODE_LEARNED) return IVM_ERR_ARG;
     if (p->tile < 0 || p->warps_per_block < 0 || p->warps_per_block > 4) return IVM_ERR_ARG;
     if (p->table_tile < 0) return IVM_ERR_ARG;
+    if (p->proof_tile < 0 || p->proof_tile > (1 << 16)) return IVM_ERR_ARG;
     return IVM_OK;
 }
 
@@ -171,6 +172,7 @@ LaunchCfg launch_cfg(const ivm_ctx *c, const ivm_params *p)
     L.cache = (p->flags & IVM_FLAG_OCCLUDER_CACHE) != 0;
     L.dedup = (p->flags & IVM_FLAG_DEDUP_SOURCES) != 0;
     L.aligned = (p->flags & IVM_FLAG_ALIGNED_FACETS) != 0;
+    L.proof_tile = p->proof_tile > 0 ? p->proof_tile : 32;
     return L;
 }
 
@@ -420,6 +422,7 @@ void key_params(std::vector<unsigned long long> &k, const ivm_params *p)
     k.push_back((unsigned long long)p->warps_per_block);
     k.push_back((unsigned long long)p->flags);
     k.push_back((unsigned long long)p->table_tile);
+    k.push_back((unsigned long long)p->proof_tile);
 }
 
 }  // namespace
@@ -1567,6 +1570,7 @@ extern "C" int ivm_autotune(ivm_ctx *c, const ivm_scene *scenes, int32_t n_scene
     const int wpbs[] = {2, 4};
     const int mtiles[] = {1, 2, 4, 8, 16, 32, 64};
     const int ttiles[] = {8, 16, 32, 64, 128, 256, 512, 1024, 2048};
+    const int ptiles[] = {16, 64, 128};   // stretch lengths tried besides the default 32
     float best_total = 1e30f;
     ivm_params best = *params;
     for (int wpb : wpbs) {
@@ -1603,13 +1607,31 @@ extern "C" int ivm_autotune(ivm_ctx *c, const ivm_scene *scenes, int32_t n_scene
                 first = false;
             }
             p.table_tile = tt;
+            // then the stretch length at that item size
+            int pt = base.proof_tile > 0 ? base.proof_tile : 32;
+            for (int ptile : ptiles) {
+                p.proof_tile = ptile;
+                ivm_stats st;
+                float ms = 1e30f;
+                for (int rep = 0; rep < 3; rep++) {
+                    if ((r = ivm_build_table(c, scenes, ns, &p, tx, rx, snaps.data(), tout.data(),
+                                             lout.data(), &st)))
+                        return r;
+                    if (rep == 1 || (rep > 1 && st.ms_traverse > ms)) ms = st.ms_traverse;
+                }
+                if (ms < bt) { bt = ms; pt = ptile; }
+            }
+            p.proof_tile = pt;
         }
         if (bm + bt < best_total) {
             best_total = bm + bt;
             best = *params;
             best.warps_per_block = wpb;
             best.tile = mt;
-            if (with_table) best.table_tile = tt;
+            if (with_table) {
+                best.table_tile = tt;
+                best.proof_tile = p.proof_tile;
+            }
         }
     }
     *params = best;

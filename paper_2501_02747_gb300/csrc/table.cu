@@ -61,8 +61,8 @@ constexpr bool kTableBatchProbe = true;
 // Per-sample temporal blockers (shared memory, 32 facets x 32 samples per warp).
 constexpr bool kTableSampleBlockers = true;
 constexpr int kSampleSlots = 32 * 32;
-// Snapshots per straight-stretch proof (a work item may hold several).
-constexpr int kProofTile = 32;
+// Snapshots per straight-stretch proof (a work item may hold several) come
+// from the launch (PT, ivm_params.proof_tile).
 
 // ------------------------------------------------------------ lazy splitting
 
@@ -396,7 +396,7 @@ __device__ __noinline__ bool tile_on_segment(const int *pos, long long t0, long 
 // Snapshots [tb, te) of work item `item` (tb < 0: the item's whole tile).
 // With a slot, the range's end is re-read from it at every stretch.
 template <bool CACHE, class LeafFn>
-__device__ __noinline__ void table_tile(const DevScenes &g, long long item, int TT,
+__device__ __noinline__ void table_tile(const DevScenes &g, long long item, int TT, int PT,
                                            long long tb, long long te, StealSlot *slot,
                                            const int *rep, int *err, WalkCounters &wc,
                                            LeafFn leaf, OccluderCache &cache, int *sblk)
@@ -436,14 +436,14 @@ __device__ __noinline__ void table_tile(const DevScenes &g, long long item, int 
         for (int i = lane; i < kSampleSlots; i += 32) sblk[i] = -1;
         __syncwarp();
     }
-    for (long long u0 = t0; u0 < t1; u0 += kProofTile) {   // straight-stretch proofs
+    for (long long u0 = t0; u0 < t1; u0 += PT) {   // straight-stretch proofs
         if (slot) {
             long long end = 0;
             if (lane == 0) end = slot_publish(slot, u0);
             t1 = min(t1, __shfl_sync(kFull, end, 0));
             if (u0 >= t1) break;
         }
-        const long long u1 = min(u0 + (long long)kProofTile, t1);
+        const long long u1 = min(u0 + (long long)PT, t1);
         if (rep) {   // a stretch whose rows are all copied later needs nothing
             bool traced = false;
             for (long long t = u0 + lane; t < u1; t += 32)
@@ -648,10 +648,10 @@ constexpr int kTableMinBlocks = IVM_TABLE_MIN_BLOCKS;
 // loads may be stale or torn: they only propose the compare value of the
 // swap, which then fails.
 constexpr int kStealWindow = 256;
-constexpr int kStealMin = 2 * kProofTile;   // smallest remaining range worth splitting
+// The smallest remaining range worth splitting is two stretches (2 PT).
 
 template <bool CACHE, class LeafFn>
-__device__ __forceinline__ void steal_loop(const DevScenes &g, int TT, StealSlot *slots,
+__device__ __forceinline__ void steal_loop(const DevScenes &g, int TT, int PT, StealSlot *slots,
                                            StealSlot *mine, const int *rep, int *err,
                                            WalkCounters &wc, LeafFn leaf, OccluderCache &cache,
                                            int *sblk)
@@ -691,7 +691,7 @@ __device__ __forceinline__ void steal_loop(const DevScenes &g, int TT, StealSlot
                 best_rem = r2; best = i2; sa = a2; sb = b2;
             }
         }
-        if (best_rem < kStealMin) {
+        if (best_rem < 2LL * PT) {
             if (full) return;
             full = true;   // nothing in this window: look at all slots once
             continue;
@@ -699,7 +699,7 @@ __device__ __forceinline__ void steal_loop(const DevScenes &g, int TT, StealSlot
         full = nslots <= kStealWindow;
         const long long cur = (long long)(unsigned)sb, end = (long long)(sb >> 32);
         const long long half = best_rem / 2;
-        const long long mid = cur + (half + kProofTile - 1) / kProofTile * kProofTile;
+        const long long mid = cur + (half + PT - 1) / PT * PT;
         bool ok = false;
         if (lane == 0) {
             const StealSlot seen{sa, sb};
@@ -707,14 +707,14 @@ __device__ __forceinline__ void steal_loop(const DevScenes &g, int TT, StealSlot
             if (ok) slot_start(mine, (long long)sa - 1, mid, end);
         }
         if (!__shfl_sync(kFull, ok, 0)) continue;
-        table_tile<CACHE>(g, (long long)sa - 1, TT, mid, end, mine, rep, err, wc, leaf, cache,
-                          sblk);
+        table_tile<CACHE>(g, (long long)sa - 1, TT, PT, mid, end, mine, rep, err, wc, leaf,
+                          cache, sblk);
     }
 }
 
 template <bool PERSIST, bool CACHE, class LeafFn>
 __global__ void __launch_bounds__(kTravThreads, kTableMinBlocks)
-k_table(DevScenes g, long long total_items, long long all_items, int TT,
+k_table(DevScenes g, long long total_items, long long all_items, int TT, int PT,
                         const int *rep, unsigned long long *work, StealSlot *slots,
                         unsigned long long *ctr, int *err)
 {
@@ -729,7 +729,7 @@ k_table(DevScenes g, long long total_items, long long all_items, int TT,
                           : nullptr;
     auto run = [&](long long it) {
         if (it < total_items)
-            table_tile<CACHE>(g, it, TT, -1, -1, mine, rep, err, wc, leaf, cache, sblk);
+            table_tile<CACHE>(g, it, TT, PT, -1, -1, mine, rep, err, wc, leaf, cache, sblk);
         else los_item<CACHE>(g, it - total_items, err, wc, leaf, cache);
     };
     if (!PERSIST) {
@@ -743,7 +743,7 @@ k_table(DevScenes g, long long total_items, long long all_items, int TT,
             if ((long long)base >= all_items) break;
             run((long long)base);
         }
-        if (mine) steal_loop<CACHE>(g, TT, slots, mine, rep, err, wc, leaf, cache, sblk);
+        if (mine) steal_loop<CACHE>(g, TT, PT, slots, mine, rep, err, wc, leaf, cache, sblk);
     }
     flush_counters(wc, ctr);
 }
@@ -827,11 +827,12 @@ static void launch_one(const DevScenes &g, long long items, long long all, int T
             slots = static_cast<StealSlot *>(cfg.steal);
             cudaMemsetAsync(slots, 0, sizeof(StealSlot) * (size_t)warps, st);
         }
-        kern<<<blocks, threads, smem, st>>>(g, items, all, TT, rep, work, slots, ctr, err);
+        kern<<<blocks, threads, smem, st>>>(g, items, all, TT, cfg.proof_tile, rep, work, slots,
+                                            ctr, err);
     } else {
         long long blocks = (all + cfg.warps_per_block - 1) / cfg.warps_per_block;
-        kern<<<(unsigned)blocks, threads, smem, st>>>(g, items, all, TT, rep, work, nullptr, ctr,
-                                                      err);
+        kern<<<(unsigned)blocks, threads, smem, st>>>(g, items, all, TT, cfg.proof_tile, rep, work,
+                                                      nullptr, ctr, err);
     }
 }
 

@@ -36,7 +36,7 @@ class ivm_params(ctypes.Structure):
     _fields_ = [("samples_per_side", ctypes.c_int32), ("max_order", ctypes.c_int32),
                 ("mode", ctypes.c_int32), ("tile", ctypes.c_int32),
                 ("warps_per_block", ctypes.c_int32), ("flags", ctypes.c_int32),
-                ("table_tile", ctypes.c_int32)]
+                ("table_tile", ctypes.c_int32), ("proof_tile", ctypes.c_int32)]
 
 
 class ivm_stats(ctypes.Structure):
@@ -279,8 +279,9 @@ class Context:
         self.close()
 
 
-def _params(s, K=0, mode=IVM_MODE_EXACT, tile=0, warps_per_block=0, flags=0, table_tile=0):
-    return ivm_params(s, K, mode, tile, warps_per_block, flags, table_tile)
+def _params(s, K=0, mode=IVM_MODE_EXACT, tile=0, warps_per_block=0, flags=0, table_tile=0,
+            proof_tile=0):
+    return ivm_params(s, K, mode, tile, warps_per_block, flags, table_tile, proof_tile)
 
 
 def ivm_autotune(ctx, facets, s, tx=None, rx=None, mode=IVM_MODE_FILTERED, flags=0):
@@ -306,7 +307,8 @@ def ivm_autotune(ctx, facets, s, tx=None, rx=None, mode=IVM_MODE_FILTERED, flags
     else:
         _check(lib().ivm_autotune(ctx.handle, scenes, len(flist), None, None, None,
                                   ctypes.byref(p)), "ivm_autotune")
-    return {"tile": p.tile, "warps_per_block": p.warps_per_block, "table_tile": p.table_tile}
+    return {"tile": p.tile, "warps_per_block": p.warps_per_block, "table_tile": p.table_tile,
+            "proof_tile": p.proof_tile}
 
 
 def _scenes(facet_list):
@@ -521,7 +523,7 @@ def ivm_visibility_ranges(ctx, facets, s, tx, rx, table, count_only=False):
 
 
 def ivm_build_table(ctx, facets, s, tx, rx, mode=IVM_MODE_EXACT, flags=0, tile=0,
-                    warps_per_block=0, out=None):
+                    warps_per_block=0, out=None, proof_tile=0):
     """Table of one scene or a list of scenes: (table [S][2][W], los [S]) per scene."""
     import torch
     single = not isinstance(facets, (list, tuple))
@@ -553,7 +555,7 @@ def ivm_build_table(ctx, facets, s, tx, rx, mode=IVM_MODE_EXACT, flags=0, tile=0
     tx_p = (_VP * len(out))(*[_addr(a) for a in txs])
     rx_p = (_VP * len(out))(*[_addr(a) for a in rxs])
     st = ivm_stats()
-    p = _params(s, 0, mode, 0, warps_per_block, flags, table_tile=tile)
+    p = _params(s, 0, mode, 0, warps_per_block, flags, table_tile=tile, proof_tile=proof_tile)
     _check(lib().ivm_build_table(ctx.handle, scenes, len(flist), ctypes.byref(p), tx_p, rx_p,
                                  n_snap, tab_p, los_p, ctypes.byref(st)), "ivm_build_table")
     return (out[0] if single else out), st

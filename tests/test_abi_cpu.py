@@ -52,7 +52,7 @@ def test_strerror_is_host_only():
 
 def test_struct_layouts_match_header():
     assert ctypes.sizeof(ivm.ivm_facet) == 40
-    assert ctypes.sizeof(ivm.ivm_params) == 28
+    assert ctypes.sizeof(ivm.ivm_params) == 32
     assert ctypes.sizeof(ivm.ivm_tree_summary) == 24
     assert ctypes.sizeof(ivm.ivm_stats) == 10 * 8 + 6 * 4 + 8
     assert ctypes.sizeof(ivm.ivm_range) == 32 == ivm.RANGE_DTYPE.itemsize

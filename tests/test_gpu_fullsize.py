@@ -75,6 +75,7 @@ def bench_config(ctx, F, s, tx, rx):
                              tile=tuned["tile"], warps_per_block=tuned["warps_per_block"], out=M)
         ivm.ivm_build_table(ctx, Fd, s, txd, rxd, mode=ivm.IVM_MODE_FILTERED, flags=FAST,
                             tile=tuned["table_tile"], warps_per_block=tuned["warps_per_block"],
+                            proof_tile=tuned["proof_tile"],
                             out=(T, L))
     torch.cuda.synchronize()
     return M, T, L
@@ -207,6 +208,7 @@ def test_batch_every_scene_against_the_oracle_with_graph_replays(ctx):
                              tile=tuned["tile"], warps_per_block=tuned["warps_per_block"], out=Ms)
         ivm.ivm_build_table(ctx, Fd, s, txd, rxd, mode=ivm.IVM_MODE_FILTERED, flags=FAST,
                             tile=tuned["table_tile"], warps_per_block=tuned["warps_per_block"],
+                            proof_tile=tuned["proof_tile"],
                             out=Ts)
         torch.cuda.synchronize()
         return ivm.kernel_launches() - l0

@@ -146,19 +146,21 @@ def test_autotune_picks_a_valid_shape_and_results_stay_exact(ctx):
     p = ivm.ivm_autotune(ctx, [sc.facets for sc in scenes], 2, [sc.tx for sc in scenes],
                          [sc.rx for sc in scenes], flags=FAST)
     assert p["warps_per_block"] in (2, 4)
-    assert p["tile"] in (1, 2, 4, 8, 16) and p["table_tile"] in (4, 8, 16, 32, 64)
+    assert p["tile"] in (1, 2, 4, 8, 16, 32, 64)
+    assert p["table_tile"] in (8, 16, 32, 64, 128, 256, 512, 1024, 2048)
+    assert p["proof_tile"] in (16, 32, 64, 128)
     for sc in scenes:
         M, _ = ivm.ivm_build_matrix(ctx, sc.facets, 2, mode=ivm.IVM_MODE_FILTERED, flags=FAST,
                                     tile=p["tile"], warps_per_block=p["warps_per_block"])
         assert (to_np(M) == oracle.matrix(sc.facets, 2)).all()
         (T, L), _ = ivm.ivm_build_table(ctx, sc.facets, 2, sc.tx, sc.rx,
                                         mode=ivm.IVM_MODE_FILTERED, flags=FAST,
-                                        tile=p["table_tile"],
+                                        tile=p["table_tile"], proof_tile=p["proof_tile"],
                                         warps_per_block=p["warps_per_block"])
         tab, los = oracle.table(sc.facets, 2, sc.tx, sc.rx)
         assert (to_np(T) == tab).all() and (L.cpu().numpy() == los).all()
     m_only = ivm.ivm_autotune(ctx, scenes[0].facets, 2, flags=FAST)
-    assert m_only["tile"] in (1, 2, 4, 8, 16)
+    assert m_only["tile"] in (1, 2, 4, 8, 16, 32, 64)
 
 
 def test_many_samples_table_path(ctx):
@@ -320,7 +322,7 @@ def test_district_in_the_bench_launch_configuration(ctx, district_gpu):
                              tile=tuned["tile"], warps_per_block=tuned["warps_per_block"], out=Md)
         ivm.ivm_build_table(ctx, F, 5, tx, rx, mode=ivm.IVM_MODE_FILTERED, flags=flags,
                             tile=tuned["table_tile"], warps_per_block=tuned["warps_per_block"],
-                            out=(Td, Ld))
+                            proof_tile=tuned["proof_tile"], out=(Td, Ld))
         ivm.ivm_expand_image_tree(ctx, Md, Td, Ld, n, K, summary=Sd)
         torch.cuda.synchronize()
         assert (to_np(Md) == M).all()

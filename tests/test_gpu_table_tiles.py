@@ -88,3 +88,38 @@ def test_lazy_splitting_gives_the_same_rows(ctx, tile):
     snaps = np.arange(0, sc.n_snap, 997)
     tab, los = oracle.table(sc.facets, s, sc.tx, sc.rx, snaps=snaps)
     assert (to_np(T)[snaps] == tab).all() and (L.cpu().numpy()[snaps] == los).all()
+
+
+@pytest.mark.parametrize("seed", [1, 2])
+def test_stretch_length_gives_the_same_rows(ctx, seed):
+    """The number of snapshots per straight-stretch proof (proof_tile) is a
+    launch-shape choice: stretches of 1, 7, 16, 32, 64, 128 and 500 snapshots,
+    with and without lazy splitting, give the oracle's rows on piecewise
+    routes and on the district."""
+    rng = np.random.default_rng(950 + seed)
+    sc = sg.random_small_city(950 + seed, n_buildings=10, side=9000, n_snap=2, s=3)
+    n = 400
+    rx = route(rng, 9000, 150, n)
+    tx = route(rng, 9000, 1500, n)
+    tab, los = oracle.table(sc.facets, 3, tx, rx)
+    for pt in (1, 7, 16, 32, 64, 128, 500):
+        for flags in (FAST | ivm.IVM_FLAG_ALIGNED_FACETS, FAST | ivm.IVM_FLAG_NO_SPLIT):
+            (T, L), _ = ivm.ivm_build_table(ctx, sc.facets, 3, tx, rx, mode=ivm.IVM_MODE_FILTERED,
+                                            flags=flags, tile=200, proof_tile=pt)
+            assert (to_np(T) == tab).all(), (pt, flags)
+            assert (L.cpu().numpy() == los).all()
+    d = sg.district()
+    (T0, L0), _ = ivm.ivm_build_table(ctx, d.facets, 5, d.tx, d.rx, mode=ivm.IVM_MODE_FILTERED,
+                                      flags=FAST, tile=128)
+    for pt in (16, 64, 128):
+        (T, L), _ = ivm.ivm_build_table(ctx, d.facets, 5, d.tx, d.rx, mode=ivm.IVM_MODE_FILTERED,
+                                        flags=FAST, tile=1024, proof_tile=pt)
+        assert (to_np(T) == to_np(T0)).all() and (L.cpu().numpy() == L0.cpu().numpy()).all()
+
+
+def test_stretch_length_out_of_range_is_refused(ctx):
+    sc = sg.tiny()
+    for pt in (-1, (1 << 16) + 1):
+        with pytest.raises(ivm.IvmError):
+            ivm.ivm_build_table(ctx, sc.facets, 3, sc.tx, sc.rx, mode=ivm.IVM_MODE_FILTERED,
+                                flags=FAST, proof_tile=pt)

@@ -78,8 +78,8 @@ def parse():
     p.add_argument("--rows", type=int, default=None,
                    help="profiling: decide only the pairs of the first ROWS matrix rows")
     p.add_argument("--shape", default=None,
-                   help="profiling: launch shape tile,warps_per_block,table_tile[,proof_tile] "
-                        "instead of the autotuner's")
+                   help="profiling: launch shape tile,warps_per_block,table_tile[,proof_tile"
+                        "[,corner proof 0/1]] instead of the autotuner's")
     return p.parse_args()
 
 
@@ -300,7 +300,8 @@ class Path:
         self.T = torch.empty((S, 2, self.W), dtype=torch.int32, device=dev)
         self.L = torch.empty((S,), dtype=torch.uint8, device=dev)
         self.summ = torch.empty((S, self.K + 1, 3), dtype=torch.int64, device=dev)
-        fast = fast_flags(ivm)
+        # the autotuner's choice of the matrix's corner proof joins the fast flags
+        fast = fast_flags(ivm) | (tuned.get("flags", 0) & ivm.IVM_FLAG_NO_CORNER_PROOF)
         self.forms = {"plain": dict(mode=ivm.IVM_MODE_EXACT, flags=0),
                       "fast": dict(mode=ivm.IVM_MODE_FILTERED, flags=fast),
                       "fast_edge_filter": dict(mode=ivm.IVM_MODE_FILTERED,
@@ -452,7 +453,8 @@ def profile_case(args, ivm, shard, sg, ctx, dev, stream):
     if args.shape:
         v = [int(x) for x in args.shape.split(",")]
         tuned = {"tile": v[0], "warps_per_block": v[1], "table_tile": v[2],
-                 "proof_tile": v[3] if len(v) > 3 else 0}
+                 "proof_tile": v[3] if len(v) > 3 else 0,
+                 "flags": ivm.IVM_FLAG_NO_CORNER_PROOF if len(v) > 4 and v[4] == 0 else 0}
     else:
         tuned = ivm.ivm_autotune(ctx, fd, sc.samples_per_side, tx, rx,
                                  mode=ivm.IVM_MODE_FILTERED, flags=fast_flags(ivm))
@@ -649,6 +651,7 @@ def batch_block(args, ivm, sg, ctx, dev, stream, flush):
                torch.empty((x.n_snap,), dtype=torch.uint8, device=dev)) for x in scenes]
         return Ms, Ts
 
+    fast |= tuned["flags"] & ivm.IVM_FLAG_NO_CORNER_PROOF
     forms = {"fast": (dict(mode=ivm.IVM_MODE_FILTERED, flags=fast,
                            tile=tuned["tile"], warps_per_block=tuned["warps_per_block"]),
                       dict(mode=ivm.IVM_MODE_FILTERED, flags=fast,

@@ -86,6 +86,10 @@ extern "C" {
                                      error bound and exact int64 where it cannot decide,
                                      in place of the four-edge FP32 filter; other facets
                                      keep the filter.  Same bits; not in the paper */
+#define IVM_FLAG_NO_CORNER_PROOF 64 /* matrix, with OCCLUDER_CACHE: do not try to settle a
+                                     hidden pair from its 16 corner-sample segments before
+                                     its packets (a schedule choice: same bits; the
+                                     autotuner sets or clears it); not in the paper */
 
 typedef struct ivm_facet {
     int32_t o[3], u[3], v[3]; /* cm; u x v points outward */
@@ -386,7 +390,8 @@ int ivm_ranker_gradients(ivm_ctx *ctx, const float *weights, const float *x, con
  * workload -- the first 8 scenes at most and the first 16,384 snapshots of
  * each -- with params' samples_per_side, mode and flags (graph replay is
  * switched off while timing), and writes the fastest warps_per_block, tile,
- * table_tile and proof_tile into *params.  Inputs as for ivm_build_table (host or
+ * table_tile and proof_tile into *params, and sets or clears
+ * IVM_FLAG_NO_CORNER_PROOF in params->flags (the other flags are kept).  Inputs as for ivm_build_table (host or
  * device; tx, rx, n_snap may be NULL to tune the matrix only).  The outputs
  * of the trial runs go to the context's scratch.  Errors: as
  * ivm_build_table. */

@@ -173,6 +173,7 @@ LaunchCfg launch_cfg(const ivm_ctx *c, const ivm_params *p)
     L.dedup = (p->flags & IVM_FLAG_DEDUP_SOURCES) != 0;
     L.aligned = (p->flags & IVM_FLAG_ALIGNED_FACETS) != 0;
     L.proof_tile = p->proof_tile > 0 ? p->proof_tile : 32;
+    L.corner = (p->flags & IVM_FLAG_NO_CORNER_PROOF) == 0;
     return L;
 }
 
@@ -1591,6 +1592,18 @@ extern "C" int ivm_autotune(ivm_ctx *c, const ivm_scene *scenes, int32_t n_scene
             first = false;
         }
         p.tile = mt;
+        // then the corner proof the other way at that tile (same bits either way)
+        {
+            ivm_params q = p;
+            q.flags ^= IVM_FLAG_NO_CORNER_PROOF;
+            ivm_stats st;
+            float ms = 1e30f;
+            for (int rep = 0; rep < 3; rep++) {
+                if ((r = ivm_build_matrix(c, scenes, ns, &q, mout.data(), &st))) return r;
+                if (rep == 1 || (rep > 1 && st.ms_traverse > ms)) ms = st.ms_traverse;
+            }
+            if (ms < bm) { bm = ms; p.flags = q.flags; }
+        }
         if (with_table) {
             first = true;
             for (int tile : ttiles) {
@@ -1628,6 +1641,8 @@ extern "C" int ivm_autotune(ivm_ctx *c, const ivm_scene *scenes, int32_t n_scene
             best = *params;
             best.warps_per_block = wpb;
             best.tile = mt;
+            best.flags = (params->flags & ~IVM_FLAG_NO_CORNER_PROOF) |
+                         (p.flags & IVM_FLAG_NO_CORNER_PROOF);
             if (with_table) {
                 best.table_tile = tt;
                 best.proof_tile = p.proof_tile;

@@ -134,6 +134,7 @@ struct LaunchCfg {
     int dedup;            // table: compute one row per run of equal source positions
     int aligned = 0;      // filtered forms: exact test for axis-aligned rectangle facets
     int proof_tile = 32;  // table: snapshots per straight-stretch proof
+    int corner = 1;       // matrix: try the corner proof before the packets
     const unsigned long long *count_dev = nullptr;  // matrix, persistent: device pair count
     LearnedDev learn;     // matrix, learned form (ranks == nullptr: off)
     void *steal = nullptr;// table, persistent: 16-byte slots, 64 per SM (nullptr: no splitting)

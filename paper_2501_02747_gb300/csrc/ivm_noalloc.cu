@@ -198,6 +198,7 @@ extern "C" int ivm_build_matrix_noalloc(const ivm_facet *facets, int32_t n_facet
     cfg.cache = (params->flags & IVM_FLAG_OCCLUDER_CACHE) != 0;
     cfg.dedup = 0;
     cfg.aligned = (params->flags & IVM_FLAG_ALIGNED_FACETS) != 0;
+    cfg.corner = (params->flags & IVM_FLAG_NO_CORNER_PROOF) == 0;
     NA_CK(launch_matrix(g, pairs, npairs, cfg, misc + 2, ctr, err, st));
     return noalloc_error(base, st);
 }

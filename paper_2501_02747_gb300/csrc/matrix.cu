@@ -77,7 +77,10 @@ __device__ __forceinline__ unsigned occlude_ranked(Seg &s, unsigned alive, const
 // each sample q the p-set contains i's corners, hence all of i's samples.
 // Candidates F are the warp's recent occluders; lanes 0-15 test one, 16-31
 // another, with the same exact facet test as everywhere else.
-constexpr bool kMatrixCornerProof = true;
+// The proof is tried unless IVM_FLAG_NO_CORNER_PROOF is given: it pays where
+// one facet often hides a whole pair (district: matrix 1.18 ms with it, 1.21
+// without; degenerate district 1.26 / 1.31) and costs more than it settles
+// on the 25k-facet city (315 / 296 ms); the autotuner chooses.
 
 template <class LeafFn>
 __device__ __noinline__ bool corners_blocked(const DevScenes &g, int baseI, int baseJ, int s,
@@ -109,7 +112,7 @@ template <bool CACHE, bool LEARN, class LeafFn>
 __device__ __forceinline__ void decide_pair(const DevScenes &g, int gi, int gj,
                                             const LearnedDev &lrn, unsigned long long rk,
                                             int *err, WalkCounters &wc, LeafFn leaf,
-                                            OccluderCache &cache)
+                                            OccluderCache &cache, bool corner)
 {
     const int lane = threadIdx.x & 31;
     const Leaf Li = load_leaf(g.leaf, gi), Lj = load_leaf(g.leaf, gj);
@@ -122,7 +125,7 @@ __device__ __forceinline__ void decide_pair(const DevScenes &g, int gi, int gj,
     const float diry = (float)(2 * (Lj.oy - Li.oy) + Lj.uy + Lj.vy - Li.uy - Li.vy);
     const float dirz = (float)(2 * (Lj.oz - Li.oz) + Lj.uz + Lj.vz - Li.uz - Li.vz);
     const int budget = D.budget;
-    if (CACHE && kMatrixCornerProof && cache.f[0] >= 0 &&
+    if (CACHE && corner && cache.f[0] >= 0 &&
         corners_blocked(g, baseI, baseJ, s, cache.f[0], cache.f[1], cache.f[2], cache.f[3], wc,
                         leaf))
         return;
@@ -155,7 +158,7 @@ __device__ __forceinline__ void decide_pair(const DevScenes &g, int gi, int gj,
             break;
         }
         // the first blocked packet may have brought a new occluder to the front
-        if (CACHE && kMatrixCornerProof && !retried && b0 + 32 < total) {
+        if (CACHE && corner && !retried && b0 + 32 < total) {
             retried = true;
             const int f = cache.f[0];
             if (f >= 0 && corners_blocked(g, baseI, baseJ, s, f, -1, -1, -1, wc, leaf)) return;
@@ -184,7 +187,7 @@ constexpr int kMatrixMinBlocks = IVM_MATRIX_MIN_BLOCKS,
 
 template <bool PERSIST, bool CACHE, bool LEARN, class LeafFn>
 __global__ void __launch_bounds__(kTravThreads, LEARN ? kMatrixMinBlocksLearned : kMatrixMinBlocks)
-k_matrix(DevScenes g, const int2 *pairs, unsigned long long npairs, int tile,
+k_matrix(DevScenes g, const int2 *pairs, unsigned long long npairs, int tile, int corner,
          const unsigned long long *count_dev, LearnedDev lrn, unsigned long long *work,
          unsigned long long *ctr, int *err)
 {
@@ -200,7 +203,7 @@ k_matrix(DevScenes g, const int2 *pairs, unsigned long long npairs, int tile,
         if (w < npairs) {
             const int2 p = pairs[w];
             decide_pair<CACHE, LEARN>(g, p.x, p.y, lrn, LEARN ? lrn.ranks[w] : 0ull, err, wc,
-                                      leaf, cache);
+                                      leaf, cache, corner != 0);
         }
     } else {
         for (;;) {
@@ -212,7 +215,7 @@ k_matrix(DevScenes g, const int2 *pairs, unsigned long long npairs, int tile,
             for (unsigned long long w = base; w < end; w++) {
                 const int2 p = pairs[w];
                 decide_pair<CACHE, LEARN>(g, p.x, p.y, lrn, LEARN ? lrn.ranks[w] : 0ull, err,
-                                          wc, leaf, cache);
+                                          wc, leaf, cache, corner != 0);
             }
         }
     }
@@ -231,12 +234,12 @@ static void launch_one(const DevScenes &g, const int2 *pairs, unsigned long long
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, 0);
         int blocks = cfg.n_sm * (per_sm > 0 ? per_sm : 1);
         cudaMemsetAsync(work, 0, sizeof(unsigned long long), st);
-        kern<<<blocks, threads, 0, st>>>(g, pairs, npairs, cfg.tile, cfg.count_dev, cfg.learn,
-                                         work, ctr, err);
+        kern<<<blocks, threads, 0, st>>>(g, pairs, npairs, cfg.tile, cfg.corner, cfg.count_dev,
+                                         cfg.learn, work, ctr, err);
     } else {
         unsigned long long blocks = (npairs + cfg.warps_per_block - 1) / cfg.warps_per_block;
-        kern<<<(unsigned)blocks, threads, 0, st>>>(g, pairs, npairs, 1, nullptr, cfg.learn, work,
-                                                   ctr, err);
+        kern<<<(unsigned)blocks, threads, 0, st>>>(g, pairs, npairs, 1, cfg.corner, nullptr,
+                                                   cfg.learn, work, ctr, err);
     }
 }
 

@@ -21,6 +21,7 @@ IVM_MODE_EXACT, IVM_MODE_FILTERED, IVM_MODE_LEARNED = 0, 1, 2
 IVM_FLAG_PERSISTENT, IVM_FLAG_GRAPH, IVM_FLAG_OCCLUDER_CACHE, IVM_FLAG_DEDUP_SOURCES = 1, 2, 4, 8
 IVM_FLAG_NO_SPLIT = 16
 IVM_FLAG_ALIGNED_FACETS = 32
+IVM_FLAG_NO_CORNER_PROOF = 64
 
 
 class ivm_facet(ctypes.Structure):
@@ -308,7 +309,7 @@ def ivm_autotune(ctx, facets, s, tx=None, rx=None, mode=IVM_MODE_FILTERED, flags
         _check(lib().ivm_autotune(ctx.handle, scenes, len(flist), None, None, None,
                                   ctypes.byref(p)), "ivm_autotune")
     return {"tile": p.tile, "warps_per_block": p.warps_per_block, "table_tile": p.table_tile,
-            "proof_tile": p.proof_tile}
+            "proof_tile": p.proof_tile, "flags": p.flags}
 
 
 def _scenes(facet_list):

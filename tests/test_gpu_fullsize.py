@@ -65,15 +65,17 @@ def bench_config(ctx, F, s, tx, rx):
     txd = torch.from_numpy(np.ascontiguousarray(tx)).cuda()
     rxd = torch.from_numpy(np.ascontiguousarray(rx)).cuda()
     tuned = ivm.ivm_autotune(ctx, Fd, s, txd, rxd, mode=ivm.IVM_MODE_FILTERED, flags=FAST)
+    flags = tuned["flags"]          # FAST, with the autotuner's corner-proof choice
+    assert flags & ~ivm.IVM_FLAG_NO_CORNER_PROOF == FAST
     n, S = F.shape[0], tx.shape[0]
     W = ivm.words(n)
     M = torch.empty((n, W), dtype=torch.int32, device="cuda")
     T = torch.empty((S, 2, W), dtype=torch.int32, device="cuda")
     L = torch.empty((S,), dtype=torch.uint8, device="cuda")
     for _ in range(2):
-        ivm.ivm_build_matrix(ctx, Fd, s, mode=ivm.IVM_MODE_FILTERED, flags=FAST,
+        ivm.ivm_build_matrix(ctx, Fd, s, mode=ivm.IVM_MODE_FILTERED, flags=flags,
                              tile=tuned["tile"], warps_per_block=tuned["warps_per_block"], out=M)
-        ivm.ivm_build_table(ctx, Fd, s, txd, rxd, mode=ivm.IVM_MODE_FILTERED, flags=FAST,
+        ivm.ivm_build_table(ctx, Fd, s, txd, rxd, mode=ivm.IVM_MODE_FILTERED, flags=flags,
                             tile=tuned["table_tile"], warps_per_block=tuned["warps_per_block"],
                             proof_tile=tuned["proof_tile"],
                             out=(T, L))
@@ -204,7 +206,7 @@ def test_batch_every_scene_against_the_oracle_with_graph_replays(ctx):
 
     def call():
         l0 = ivm.kernel_launches()
-        ivm.ivm_build_matrix(ctx, Fd, s, mode=ivm.IVM_MODE_FILTERED, flags=FAST,
+        ivm.ivm_build_matrix(ctx, Fd, s, mode=ivm.IVM_MODE_FILTERED, flags=tuned["flags"],
                              tile=tuned["tile"], warps_per_block=tuned["warps_per_block"], out=Ms)
         ivm.ivm_build_table(ctx, Fd, s, txd, rxd, mode=ivm.IVM_MODE_FILTERED, flags=FAST,
                             tile=tuned["table_tile"], warps_per_block=tuned["warps_per_block"],

@@ -19,7 +19,8 @@ MODES = [ivm.IVM_MODE_EXACT, ivm.IVM_MODE_FILTERED]
 FAST = ivm.IVM_FLAG_PERSISTENT | ivm.IVM_FLAG_OCCLUDER_CACHE | ivm.IVM_FLAG_DEDUP_SOURCES
 ALIGNED = ivm.IVM_FLAG_ALIGNED_FACETS
 FLAG_SETS = [0, ivm.IVM_FLAG_PERSISTENT, ivm.IVM_FLAG_OCCLUDER_CACHE,
-             ivm.IVM_FLAG_DEDUP_SOURCES, FAST, ALIGNED, FAST | ALIGNED]
+             ivm.IVM_FLAG_DEDUP_SOURCES, FAST, ALIGNED, FAST | ALIGNED,
+             FAST | ALIGNED | ivm.IVM_FLAG_NO_CORNER_PROOF]
 
 
 @pytest.fixture(scope="module")
@@ -149,9 +150,11 @@ def test_autotune_picks_a_valid_shape_and_results_stay_exact(ctx):
     assert p["tile"] in (1, 2, 4, 8, 16, 32, 64)
     assert p["table_tile"] in (8, 16, 32, 64, 128, 256, 512, 1024, 2048)
     assert p["proof_tile"] in (16, 32, 64, 128)
+    assert p["flags"] & ~ivm.IVM_FLAG_NO_CORNER_PROOF == FAST
     for sc in scenes:
-        M, _ = ivm.ivm_build_matrix(ctx, sc.facets, 2, mode=ivm.IVM_MODE_FILTERED, flags=FAST,
-                                    tile=p["tile"], warps_per_block=p["warps_per_block"])
+        M, _ = ivm.ivm_build_matrix(ctx, sc.facets, 2, mode=ivm.IVM_MODE_FILTERED,
+                                    flags=p["flags"], tile=p["tile"],
+                                    warps_per_block=p["warps_per_block"])
         assert (to_np(M) == oracle.matrix(sc.facets, 2)).all()
         (T, L), _ = ivm.ivm_build_table(ctx, sc.facets, 2, sc.tx, sc.rx,
                                         mode=ivm.IVM_MODE_FILTERED, flags=FAST,

@@ -76,7 +76,8 @@ struct ivm_ctx {
     unsigned long long arena_gen = 1;     // bumps whenever a buffer moves
     int *d_err = nullptr;                 // device error word
     unsigned long long *d_ctr = nullptr;  // C_COUNT_ counters
-    unsigned long long *d_misc = nullptr; // [0] pair count, [1] cursor, [2] work queue
+    unsigned long long *d_misc = nullptr; // [0] pair count, [1] emit cursor (the count when the
+                                          // list holds every pair), [2] work queue
     void *d_steal = nullptr;              // table: lazy-splitting slots, 64 x 16 B per SM
     int *h_err = nullptr;
     unsigned long long *h_ctr = nullptr, *h_misc = nullptr;
@@ -557,24 +558,26 @@ int build_matrix(ivm_ctx *c, const ivm_scene *scenes, int32_t n_scenes, const iv
         bind_geometry(c, g);
         if ((e = enqueue_geometry(c, g, scenes, hd, desc_src, !dev_count))) return e;
         CK(cudaMemsetAsync(c->d_misc, 0, sizeof(unsigned long long) * 2, c->stream));
-        CK(launch_screen_count(g, hd.data(), c->d_misc, c->stream));
         unsigned long long npairs = (unsigned long long)upper;
-        if (!dev_count) {   // size the pair list from the count
+        if (!dev_count) {   // size the pair list from a count pass
+            CK(launch_screen_count(g, hd.data(), c->d_misc, c->stream));
             CK(cudaMemcpyAsync(c->h_misc, c->d_misc, sizeof(unsigned long long),
                                cudaMemcpyDeviceToHost, c->stream));
             CK(cudaStreamSynchronize(c->stream));
             npairs = c->h_misc[0];
             if ((e = ensure(c, S_PAIRS, sizeof(int2) * npairs))) return e;
         }
+        // with the list sized for every pair (dev_count), the emit pass's final
+        // cursor is the count, and the traversal reads it from device memory
         CK(launch_screen_emit(g, hd.data(), ptr<int2>(c, S_PAIRS), c->d_misc + 1, npairs,
                               c->stream));
-        CK(cudaMemcpyAsync(c->d_ctr + C_CAND_PAIRS, c->d_misc, sizeof(unsigned long long),
+        CK(cudaMemcpyAsync(c->d_ctr + C_CAND_PAIRS, c->d_misc + 1, sizeof(unsigned long long),
                            cudaMemcpyDeviceToDevice, c->stream));
         CK(record(c, 3));
         for (int k = 0; k < n_scenes; k++)
             CK(cudaMemsetAsync(hd[k].matrix, 0, sizeof(uint32_t) * hd[k].n * hd[k].W, c->stream));
         LaunchCfg cfg = cfg0;
-        cfg.count_dev = dev_count ? c->d_misc : nullptr;
+        cfg.count_dev = dev_count ? c->d_misc + 1 : nullptr;
         if (learned) {   // rank the clusters of every candidate pair
             if (!dev_count && (e = ensure(c, S_RANKS, sizeof(unsigned long long) * npairs)))
                 return e;

@@ -64,6 +64,10 @@ struct GraphEntry {
 };
 
 constexpr int kMaxGraphs = 8;
+// Host-resident tables of one scene leave in snapshot chunks of at least
+// kOutChunkMin snapshots, at most kMaxOutChunks of them.
+constexpr int kMaxOutChunks = 8;
+constexpr long long kOutChunkMin = 8192;
 constexpr long long kDevCountMaxPairs = 1LL << 31;   // upper-bound pair list cap (16 GB)
 
 }  // namespace
@@ -85,6 +89,8 @@ struct ivm_ctx {
     std::vector<GraphEntry> graphs;
     unsigned long long uses = 0;
     cudaStream_t cap = nullptr;           // private stream used only for capture
+    cudaStream_t out = nullptr;           // device-to-host copies of table chunks
+    cudaEvent_t out_ev[kMaxOutChunks] = {};
     // learned ranking: FP32 master weights, Adam moments, BF16 inference copy
     float *r_master = nullptr, *r_m = nullptr, *r_v = nullptr, *r_grads = nullptr;
     __nv_bfloat16 *r_wt = nullptr;
@@ -427,6 +433,79 @@ void key_params(std::vector<unsigned long long> &k, const ivm_params *p)
     k.push_back((unsigned long long)p->proof_tile);
 }
 
+// Table of one scene whose table or LoS lives on the host, traversed in
+// n_out snapshot chunks: the rows of chunk q are copied out on the context's
+// second stream while chunk q + 1 is traversed.  Every copy has landed when
+// this returns, whatever the outcome.
+int table_in_chunks(ivm_ctx *c, DevScenes &g, const ivm_scene *scenes,
+                    const std::vector<SceneDesc> &hd, const LaunchCfg &cfg, const int32_t *tx,
+                    const int32_t *rx, bool tx_staged, bool rx_staged, uint32_t *table,
+                    uint8_t *los, bool tab_host, bool los_host, int snap_tile,
+                    long long chunk_len, int n_out, ivm_stats *stats)
+{
+    const SceneDesc &F = hd[0];
+    const long long S = F.nsnap;
+    std::vector<SceneDesc> dq(1 + n_out, F);
+    for (int q = 0; q < n_out; q++) {
+        const long long a = q * chunk_len;
+        SceneDesc &D = dq[1 + q];
+        D.snap0 = 0;
+        D.los0 = 0;
+        D.item0 = 0;
+        D.nsnap = std::min(chunk_len, S - a);
+        D.ntiles = (int)((D.nsnap + snap_tile - 1) / snap_tile);
+        D.tx = F.tx + 3 * a;
+        D.rx = F.rx + 3 * a;
+        D.table = F.table + (size_t)a * 2 * F.W;
+        D.los = F.los + a;
+    }
+    if (!c->out) CK(cudaStreamCreateWithFlags(&c->out, cudaStreamNonBlocking));
+    for (int q = 0; q < n_out; q++)
+        if (!c->out_ev[q]) CK(cudaEventCreateWithFlags(&c->out_ev[q], cudaEventDisableTiming));
+    bind_geometry(c, g);
+    auto enqueue = [&]() -> int {
+        const size_t bytes3 = sizeof(int) * 3 * (size_t)S;
+        if (tx_staged)
+            CK(cudaMemcpyAsync(ptr<int>(c, S_TX), tx, bytes3, cudaMemcpyHostToDevice, c->stream));
+        if (rx_staged)
+            CK(cudaMemcpyAsync(ptr<int>(c, S_RX), rx, bytes3, cudaMemcpyHostToDevice, c->stream));
+        int e;
+        if ((e = enqueue_geometry(c, g, scenes, hd, hd.data(), !cfg.persistent))) return e;
+        CK(cudaMemcpyAsync(g.desc + 1, dq.data() + 1, sizeof(SceneDesc) * n_out,
+                           cudaMemcpyHostToDevice, c->stream));
+        for (int q = 0; q < n_out; q++) {
+            const SceneDesc &D = dq[1 + q];
+            const long long a = q * chunk_len;
+            DevScenes gq = g;
+            gq.desc = g.desc + 1 + q;
+            CK(launch_table(gq, D.nsnap, 2LL * D.W * D.ntiles, (D.nsnap + 31) / 32, snap_tile,
+                            cfg, ptr<int>(c, S_REP), c->d_misc + 2, c->d_ctr, c->d_err,
+                            c->stream));
+            CK(cudaEventRecord(c->out_ev[q], c->stream));
+            CK(cudaStreamWaitEvent(c->out, c->out_ev[q], 0));
+            if (tab_host)
+                CK(cudaMemcpyAsync(table + (size_t)a * 2 * F.W, D.table,
+                                   sizeof(uint32_t) * 2 * F.W * (size_t)D.nsnap,
+                                   cudaMemcpyDeviceToHost, c->out));
+            if (los_host)
+                CK(cudaMemcpyAsync(los + a, D.los, (size_t)D.nsnap, cudaMemcpyDeviceToHost,
+                                   c->out));
+        }
+        CK(record(c, 4));
+        return IVM_OK;
+    };
+    int r = enqueue();
+    // the copies wait only for chunks that were enqueued, so this ends
+    const cudaError_t e_out = cudaStreamSynchronize(c->out);
+    if (r) {
+        cudaStreamSynchronize(c->stream);
+        return r;
+    }
+    if ((r = read_error(c))) return r;
+    if (e_out != cudaSuccess) return IVM_ERR_CUDA;
+    return fill_stats(c, stats, 2ull * F.n * (unsigned long long)S, 2);
+}
+
 }  // namespace
 
 // ============================================================================ ABI
@@ -480,6 +559,9 @@ extern "C" int ivm_destroy(ivm_ctx *c)
     cudaStreamSynchronize(c->stream);
     for (auto &e : c->graphs) drop_graph(e);
     if (c->cap) cudaStreamDestroy(c->cap);
+    if (c->out) cudaStreamDestroy(c->out);
+    for (auto &e : c->out_ev)
+        if (e) cudaEventDestroy(e);
     for (void *p : {(void *)c->r_master, (void *)c->r_m, (void *)c->r_v, (void *)c->r_grads,
                     (void *)c->r_wt})
         if (p) cudaFree(p);
@@ -694,6 +776,20 @@ extern "C" int ivm_build_table(ivm_ctx *c, const ivm_scene *scenes, int32_t n_sc
     if (cfg.persistent && splittable) cfg.steal = c->d_steal;
     const bool sync_free = cfg.persistent;
     const bool use_graph = (params->flags & IVM_FLAG_GRAPH) && all_device;
+    // One scene whose table or LoS goes to the host: traverse it in snapshot
+    // chunks and copy each chunk out on a second stream while the next one is
+    // traversed.  The chunk length is a multiple of the snapshot tile, rounded
+    // up to 32 snapshots; the device holds one descriptor per chunk after the
+    // scene's own.
+    int n_out = 1;
+    long long chunk_len = 0;
+    if (n_scenes == 1 && (tab_host[0] || los_host[0]) && n_snap[0] >= 2 * kOutChunkMin) {
+        const long long unit = (snap_tile + 31LL) / 32 * 32;
+        const long long want = std::min<long long>(kMaxOutChunks, n_snap[0] / kOutChunkMin);
+        chunk_len = ((n_snap[0] + want - 1) / want + unit - 1) / unit * unit;
+        n_out = (int)((n_snap[0] + chunk_len - 1) / chunk_len);
+    }
+    if (n_out > 1 && (r = ensure(c, S_DESC, sizeof(SceneDesc) * (1 + n_out)))) return r;
     if ((r = ensure(c, S_OUT, sizeof(uint32_t) * host_tab))) return r;
     if ((r = ensure(c, S_LOS, host_los))) return r;
     if ((r = ensure(c, S_TX, sizeof(int) * pos_tx))) return r;
@@ -761,6 +857,10 @@ extern "C" int ivm_build_table(ivm_ctx *c, const ivm_scene *scenes, int32_t n_sc
                                       &ge)))
             return r;
         if ((r = replay(c, ge))) return r;
+    } else if (n_out > 1) {
+        return table_in_chunks(c, g, scenes, hd, cfg, tx[0], rx[0], tx_off[0] >= 0,
+                               rx_off[0] >= 0, table[0], los[0], tab_host[0], los_host[0],
+                               snap_tile, chunk_len, n_out, stats);
     } else {
         if ((r = enqueue(hd.data()))) return r;
     }

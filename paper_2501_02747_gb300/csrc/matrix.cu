@@ -25,6 +25,14 @@ namespace ivm {
 // Proposals walked at most before the rest of the tree.
 constexpr int kRankedWalks = 8;
 
+// Box-test form of the matrix walks (seg_box): the absolute form, one FMA
+// per plane (city, fast form: matrix 286 ms against 304 ms with the relative
+// form, the same box tests to 0.03%).
+#ifndef IVM_MATRIX_ABS_BOX
+#define IVM_MATRIX_ABS_BOX 1
+#endif
+constexpr bool kMatrixAbsBox = IVM_MATRIX_ABS_BOX != 0;
+
 // Cluster-first walk of a packet; same contract as occlude().
 template <bool CACHE, class LeafFn>
 __device__ __forceinline__ unsigned occlude_ranked(Seg &s, unsigned alive, const Node *nodes,
@@ -40,7 +48,7 @@ __device__ __forceinline__ unsigned occlude_ranked(Seg &s, unsigned alive, const
         alive = cache_tests(s, alive, leaves, wc, leaf_hit, cache, myblk);
         if (!alive) return 0;
     }
-    if (s.ix == 0.f) finish_seg(s);
+    if (s.ix == 0.f) finish_seg<kMatrixAbsBox>(s);
     unsigned long long done = 0;
     int blocker, last = -1;
     for (int k = 0; k < kRankedWalks && k < kRTop; k++) {
@@ -48,8 +56,10 @@ __device__ __forceinline__ unsigned occlude_ranked(Seg &s, unsigned alive, const
         if (c >= kRClusters || ((done >> c) & 1ull)) continue;
         if (__ldg(C + kRCStart + c + 1) <= __ldg(C + kRCStart + c)) continue;   // empty
         const unsigned before = alive;
-        alive = walk_packet(s, alive, nodes, leaves, __ldg(C + kRCut + c), dirx, diry, dirz,
-                            budget, err, wc, leaf_hit, blocker, myblk);
+        alive = walk_packet<LeafFn, NoFilter, kMatrixAbsBox>(s, alive, nodes, leaves,
+                                                             __ldg(C + kRCut + c), dirx, diry,
+                                                             dirz, budget, err, wc, leaf_hit,
+                                                             blocker, myblk);
         done |= 1ull << c;
         if (blocker >= 0) last = blocker;
         if (k == 0) wc.ranker_hits += ((before & ~alive) >> lane) & 1u;
@@ -60,8 +70,9 @@ __device__ __forceinline__ unsigned occlude_ranked(Seg &s, unsigned alive, const
         }
         if (alive == before) break;   // the proposal blocked nothing: stop trusting it
     }
-    alive = walk_packet(s, alive, nodes, leaves, root, dirx, diry, dirz, budget, err, wc,
-                        leaf_hit, blocker, myblk, CutFilter{ncl, done});
+    alive = walk_packet<LeafFn, CutFilter, kMatrixAbsBox>(s, alive, nodes, leaves, root, dirx,
+                                                          diry, dirz, budget, err, wc, leaf_hit,
+                                                          blocker, myblk, CutFilter{ncl, done});
     if (blocker >= 0) last = blocker;
     if (CACHE) cache.put(last);
     return alive;
@@ -151,8 +162,10 @@ __device__ __forceinline__ void decide_pair(const DevScenes &g, int gi, int gj,
                                           lrn.ctx + (size_t)kRCtx * Li.scene, lrn.ncl, rk, dirx,
                                           diry, dirz, budget, err, wc, leaf, cache, myblk);
         else
-            alive = occlude<CACHE>(sg, alive, g.nodes, g.leaf, D.root, dirx, diry, dirz, budget,
-                                   err, wc, leaf, cache, myblk);
+            alive = occlude<CACHE, LeafFn, CACHE, kMatrixAbsBox>(sg, alive, g.nodes, g.leaf,
+                                                                 D.root, dirx, diry, dirz,
+                                                                 budget, err, wc, leaf, cache,
+                                                                 myblk);
         if (alive) {
             visible = true;
             break;

@@ -26,8 +26,9 @@ constexpr float kBig = 3.0e38f;
 struct Seg {
     int px, py, pz;
     int dx, dy, dz;
-    float fpx, fpy, fpz;  // P as float: exact, |P| < 2^22
     float ix, iy, iz;     // round-to-nearest reciprocal of d; 2^100 where d == 0
+    float fx, fy, fz;     // box-test offsets: P as float (relative form), rn(-P i) (absolute)
+    float w;              // absolute form: widening of the box test
 };
 
 // The reciprocals are only needed by box tests; finish_seg computes them
@@ -37,33 +38,66 @@ __device__ __forceinline__ Seg make_seg(int px, int py, int pz, int qx, int qy, 
     Seg s;
     s.px = px; s.py = py; s.pz = pz;
     s.dx = qx - px; s.dy = qy - py; s.dz = qz - pz;
-    s.fpx = (float)px; s.fpy = (float)py; s.fpz = (float)pz;
     s.ix = s.iy = s.iz = 0.f;
+    s.fx = s.fy = s.fz = 0.f;
+    s.w = 0.f;
     return s;
 }
 
+template <bool ABS = false>
 __device__ __forceinline__ void finish_seg(Seg &s)
 {
     s.ix = s.dx ? __frcp_rn((float)s.dx) : 0x1p100f;
     s.iy = s.dy ? __frcp_rn((float)s.dy) : 0x1p100f;
     s.iz = s.dz ? __frcp_rn((float)s.dz) : 0x1p100f;
+    if (ABS) {
+        s.fx = __fmul_rn(-(float)s.px, s.ix);
+        s.fy = __fmul_rn(-(float)s.py, s.iy);
+        s.fz = __fmul_rn(-(float)s.pz, s.iz);
+        // an axis with d == 0 has an exact offset (p times a power of two)
+        const float e = fmaxf(fmaxf(s.dx ? fabsf(s.fx) : 0.f, s.dy ? fabsf(s.fy) : 0.f),
+                              s.dz ? fabsf(s.fz) : 0.f);
+        s.w = __fmaf_rn(e, 0x1p-22f, 0x1p-19f);
+    } else {
+        s.fx = (float)s.px; s.fy = (float)s.py; s.fz = (float)s.pz;
+    }
 }
 
 // Conservative segment-box test: true whenever the open segment touches the
-// closed integer box.  Boxes are stored enlarged by half a unit (integer
-// bound -/+ 0.5; exact in float below 2^23), which gives the d = 0 axes
-// their answer without a branch: with 1/d replaced by 2^100, an axis where
-// the segment lies inside the slab gives (-huge, +huge) and one where it lies
-// outside gives an entry above 1 or an exit below 0.  For d != 0, (l - p) is
-// exact and the product with the rounded reciprocal has relative error below
-// 2^-23; widening entry and exit by 2^-20 of their magnitude makes the test a
-// superset of the exact one.
+// closed box.  Boxes are stored enlarged by half a unit (integer bound -/+
+// 0.5; exact in float below 2^23) and only ever widened further, so no box
+// plane equals a coordinate of P.  That gives the d = 0 axes their answer
+// without a branch: with 1/d replaced by 2^100, an axis where the segment
+// lies inside the slab gives (-huge, +huge) and one where it lies outside
+// gives an entry above 1 or an exit below 0.
+//
+// Relative form: for d != 0, (l - p) is exact and the product with the
+// rounded reciprocal has relative error below 2^-23; widening entry and exit
+// by 2^-20 of their magnitude makes the test a superset of the exact one.
+//
+// Absolute form: one FMA per plane, a = rn(l i + o) with o = rn(-p i).  With
+// t = (l - p) / d, a differs from t by at most 2^-23 |t| + 2^-24 |p i| (both
+// to first order; o is exact on d = 0 axes).  If the exact segment meets the
+// box at some t in (0, 1), every axis's entry is at most t + e1 and every
+// exit at least t - e1, with e1 = 2^-23 + 2^-24 max |p i| (entries below 0
+// and exits above 1 only move further away, and the clamps to [0, 1] keep
+// t inside), so entry <= exit + 2 e1; w = 2^-19 + 2^-22 max |o| covers 2 e1,
+// the rounding of o and the rounding of exit + w.
+template <bool ABS = false>
 __device__ __forceinline__ bool seg_box(const Seg &s, float lx, float ly, float lz, float hx,
                                         float hy, float hz)
 {
-    float ax = __fmul_rn(lx - s.fpx, s.ix), bx = __fmul_rn(hx - s.fpx, s.ix);
-    float ay = __fmul_rn(ly - s.fpy, s.iy), by = __fmul_rn(hy - s.fpy, s.iy);
-    float az = __fmul_rn(lz - s.fpz, s.iz), bz = __fmul_rn(hz - s.fpz, s.iz);
+    if (ABS) {
+        float ax = __fmaf_rn(lx, s.ix, s.fx), bx = __fmaf_rn(hx, s.ix, s.fx);
+        float ay = __fmaf_rn(ly, s.iy, s.fy), by = __fmaf_rn(hy, s.iy, s.fy);
+        float az = __fmaf_rn(lz, s.iz, s.fz), bz = __fmaf_rn(hz, s.iz, s.fz);
+        float tn = fmaxf(fmaxf(fminf(ax, bx), fminf(ay, by)), fmaxf(fminf(az, bz), 0.f));
+        float tf = fminf(fminf(fmaxf(ax, bx), fmaxf(ay, by)), fminf(fmaxf(az, bz), 1.f));
+        return tn <= __fadd_rn(tf, s.w);
+    }
+    float ax = __fmul_rn(lx - s.fx, s.ix), bx = __fmul_rn(hx - s.fx, s.ix);
+    float ay = __fmul_rn(ly - s.fy, s.iy), by = __fmul_rn(hy - s.fy, s.iy);
+    float az = __fmul_rn(lz - s.fz, s.iz), bz = __fmul_rn(hz - s.fz, s.iz);
     float tn = fmaxf(fmaxf(fminf(ax, bx), fminf(ay, by)), fminf(az, bz));
     float tf = fminf(fminf(fmaxf(ax, bx), fmaxf(ay, by)), fmaxf(az, bz));
     float tnw = tn - fabsf(tn) * 0x1p-20f;
@@ -284,7 +318,7 @@ struct NoFilter {
                                          float &) const {}
 };
 
-template <class LeafFn, class Filter = NoFilter>
+template <class LeafFn, class Filter = NoFilter, bool ABS = false>
 __device__ __forceinline__ unsigned walk_packet(const Seg &s, unsigned alive, const Node *nodes,
                                                 const Leaf *leaves, int root, float dirx,
                                                 float diry, float dirz, int budget, int *err,
@@ -317,8 +351,8 @@ __device__ __forceinline__ unsigned walk_packet(const Seg &s, unsigned alive, co
             bool me = ((alive >> lane) & 1u) && filt.node(node);
             filt.grow(A.x, A.y, A.z, A.w, B.x, B.y);
             filt.grow(B.z, B.w, C.x, C.y, C.z, C.w);
-            bool hl = me && seg_box(s, A.x, A.y, A.z, A.w, B.x, B.y);
-            bool hr = me && seg_box(s, B.z, B.w, C.x, C.y, C.z, C.w);
+            bool hl = me && seg_box<ABS>(s, A.x, A.y, A.z, A.w, B.x, B.y);
+            bool hr = me && seg_box<ABS>(s, B.z, B.w, C.x, C.y, C.z, C.w);
             wc.node_tests += 2 * me;
             unsigned ml = __ballot_sync(kFull, hl), mr = __ballot_sync(kFull, hr);
             if (ml && mr) {
@@ -418,7 +452,7 @@ __device__ __forceinline__ unsigned cache_tests(const Seg &s, unsigned alive, co
     return alive;
 }
 
-template <bool CACHE, class LeafFn, bool LRU = CACHE>
+template <bool CACHE, class LeafFn, bool LRU = CACHE, bool ABS = false>
 __device__ __forceinline__ unsigned occlude(Seg &s, unsigned alive, const Node *nodes,
                                             const Leaf *leaves, int root, float dirx, float diry,
                                             float dirz, int budget, int *err, WalkCounters &wc,
@@ -429,9 +463,9 @@ __device__ __forceinline__ unsigned occlude(Seg &s, unsigned alive, const Node *
         if (!alive) return 0;
     }
     int blocker;
-    if (s.ix == 0.f) finish_seg(s);   // reciprocals only when walking
-    alive = walk_packet(s, alive, nodes, leaves, root, dirx, diry, dirz, budget, err, wc,
-                        leaf_hit, blocker, myblk);
+    if (s.ix == 0.f) finish_seg<ABS>(s);   // reciprocals only when walking
+    alive = walk_packet<LeafFn, NoFilter, ABS>(s, alive, nodes, leaves, root, dirx, diry, dirz,
+                                               budget, err, wc, leaf_hit, blocker, myblk);
     if (CACHE) cache.put(blocker);
     return alive;
 }

@@ -183,14 +183,14 @@ __device__ __forceinline__ void decide_pair(const DevScenes &g, int gi, int gj,
     }
 }
 
-// Register cap of the matrix kernel: 8 resident blocks of 128 threads (64
-// registers; a sweep of 3-12 blocks on the district and the city: more warps
-// hide the dependent box-test latency better than the spills cost; 10 and 12
-// were slower again with the out-of-line facet test).  The learned walk
-// holds more state: 6 (city, learned form: 417 ms against 445 ms with 4 and
-// 449 ms with 8).
+// Register cap of the matrix kernel: 7 resident blocks of 128 threads (72
+// registers).  With the absolute-form box test, 7 beat 8 and 6 (city, fast
+// form: 266 ms against 286 and 277 ms; district 1.19 against 1.29 ms): more
+// warps hide the dependent box-test latency, fewer registers spill more.
+// The learned walk holds more state: 6 (city, learned form: 417 ms against
+// 445 ms with 4 and 449 ms with 8).
 #ifndef IVM_MATRIX_MIN_BLOCKS
-#define IVM_MATRIX_MIN_BLOCKS 8
+#define IVM_MATRIX_MIN_BLOCKS 7
 #endif
 #ifndef IVM_MATRIX_MIN_BLOCKS_LEARNED
 #define IVM_MATRIX_MIN_BLOCKS_LEARNED 6

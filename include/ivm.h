@@ -173,6 +173,11 @@ int ivm_build_matrix_rows(ivm_ctx *ctx, const ivm_scene *scenes, int32_t n_scene
  * facets, row 1 the Rx's); los[k] receives n_snap[k] bytes, 1 if the direct
  * Tx-Rx segment is free (1 when Tx_t = Rx_t).  The matrix is not an input:
  * the table is defined by geometry, and the image tree combines the two.
+ * One scene of at least 16,384 snapshots whose table or los is host memory
+ * is traversed in up to 8 snapshot chunks, each copied to the host on a
+ * second stream of the context while the next is traversed; the call returns
+ * once every copy has landed.  After an error return the output buffers hold
+ * unspecified contents.
  * Errors: as ivm_build_matrix (IVM_ERR_RANGE also for a Tx/Rx position). */
 int ivm_build_table(ivm_ctx *ctx, const ivm_scene *scenes, int32_t n_scenes,
                     const ivm_params *params, const int32_t *const *tx,

@@ -114,3 +114,21 @@ def test_chunk_length_follows_the_tile(ctx, scene, tile):
     (T0, L0), _ = ivm.ivm_build_table(ctx, sc.facets, 3, tx, rx, out=dev_out(W), **kw)
     (T, L), _ = ivm.ivm_build_table(ctx, sc.facets, 3, tx, rx, out=host_out(W), **kw)
     assert (to_np(T) == to_np(T0)).all() and (L.numpy() == L0.cpu().numpy()).all()
+
+
+def test_error_in_a_later_chunk(ctx, scene):
+    """A receiver position out of range in the third chunk: the call reports
+    IVM_ERR_RANGE after every chunk's copy has landed, and the context then
+    gives the same rows as before."""
+    sc, rx, tx, _ = scene
+    W = ivm.words(sc.n_facets)
+    kw = dict(mode=ivm.IVM_MODE_FILTERED, flags=FAST, tile=40)
+    (T0, L0), _ = ivm.ivm_build_table(ctx, sc.facets, 3, tx, rx, out=host_out(W), **kw)
+    T0, L0 = to_np(T0).copy(), L0.numpy().copy()
+    bad = rx.copy()
+    bad[2 * CHUNK + 17] = [1 << 21, 0, 150]   # 2^21 cm x 2s is beyond the coordinate range
+    with pytest.raises(ivm.IvmError) as e:
+        ivm.ivm_build_table(ctx, sc.facets, 3, tx, bad, out=host_out(W), **kw)
+    assert e.value.code == ivm.IVM_ERR_RANGE
+    (T, L), _ = ivm.ivm_build_table(ctx, sc.facets, 3, tx, rx, out=host_out(W), **kw)
+    assert (to_np(T) == T0).all() and (L.numpy() == L0).all()

@@ -64,8 +64,8 @@ struct GraphEntry {
 };
 
 constexpr int kMaxGraphs = 8;
-// Host-resident tables of one scene leave in snapshot chunks of at least
-// kOutChunkMin snapshots, at most kMaxOutChunks of them.
+// Host-resident tables of one scene of at least 2 kOutChunkMin snapshots
+// leave in at most kMaxOutChunks snapshot chunks (ivm_build_table).
 constexpr int kMaxOutChunks = 8;
 constexpr long long kOutChunkMin = 8192;
 constexpr long long kDevCountMaxPairs = 1LL << 31;   // upper-bound pair list cap (16 GB)
@@ -434,25 +434,25 @@ void key_params(std::vector<unsigned long long> &k, const ivm_params *p)
 }
 
 // Table of one scene whose table or LoS lives on the host, traversed in
-// n_out snapshot chunks: the rows of chunk q are copied out on the context's
-// second stream while chunk q + 1 is traversed.  Every copy has landed when
-// this returns, whatever the outcome.
+// n_out snapshot chunks [cut[q], cut[q + 1]): the rows of chunk q are copied
+// out on the context's second stream while chunk q + 1 is traversed.  Every
+// copy has landed when this returns, whatever the outcome.
 int table_in_chunks(ivm_ctx *c, DevScenes &g, const ivm_scene *scenes,
                     const std::vector<SceneDesc> &hd, const LaunchCfg &cfg, const int32_t *tx,
                     const int32_t *rx, bool tx_staged, bool rx_staged, uint32_t *table,
                     uint8_t *los, bool tab_host, bool los_host, int snap_tile,
-                    long long chunk_len, int n_out, ivm_stats *stats)
+                    const std::vector<long long> &cut, int n_out, ivm_stats *stats)
 {
     const SceneDesc &F = hd[0];
     const long long S = F.nsnap;
     std::vector<SceneDesc> dq(1 + n_out, F);
     for (int q = 0; q < n_out; q++) {
-        const long long a = q * chunk_len;
+        const long long a = cut[q];
         SceneDesc &D = dq[1 + q];
         D.snap0 = 0;
         D.los0 = 0;
         D.item0 = 0;
-        D.nsnap = std::min(chunk_len, S - a);
+        D.nsnap = cut[q + 1] - a;
         D.ntiles = (int)((D.nsnap + snap_tile - 1) / snap_tile);
         D.tx = F.tx + 3 * a;
         D.rx = F.rx + 3 * a;
@@ -475,7 +475,7 @@ int table_in_chunks(ivm_ctx *c, DevScenes &g, const ivm_scene *scenes,
                            cudaMemcpyHostToDevice, c->stream));
         for (int q = 0; q < n_out; q++) {
             const SceneDesc &D = dq[1 + q];
-            const long long a = q * chunk_len;
+            const long long a = cut[q];
             DevScenes gq = g;
             gq.desc = g.desc + 1 + q;
             CK(launch_table(gq, D.nsnap, 2LL * D.W * D.ntiles, (D.nsnap + 31) / 32, snap_tile,
@@ -778,16 +778,24 @@ extern "C" int ivm_build_table(ivm_ctx *c, const ivm_scene *scenes, int32_t n_sc
     const bool use_graph = (params->flags & IVM_FLAG_GRAPH) && all_device;
     // One scene whose table or LoS goes to the host: traverse it in snapshot
     // chunks and copy each chunk out on a second stream while the next one is
-    // traversed.  The chunk length is a multiple of the snapshot tile, rounded
-    // up to 32 snapshots; the device holds one descriptor per chunk after the
-    // scene's own.
+    // traversed.  Each chunk is half of what is left (rounded up to the
+    // snapshot tile, itself rounded up to 32 snapshots) while both parts keep
+    // at least kOutChunkMin / 2 snapshots: a chunk's copy then overlaps a
+    // traversal about as long, and only the last, small copy and one tail
+    // per chunk remain exposed.  The device holds one descriptor per chunk
+    // after the scene's own.
     int n_out = 1;
-    long long chunk_len = 0;
+    std::vector<long long> cut;
     if (n_scenes == 1 && (tab_host[0] || los_host[0]) && n_snap[0] >= 2 * kOutChunkMin) {
-        const long long unit = (snap_tile + 31LL) / 32 * 32;
-        const long long want = std::min<long long>(kMaxOutChunks, n_snap[0] / kOutChunkMin);
-        chunk_len = ((n_snap[0] + want - 1) / want + unit - 1) / unit * unit;
-        n_out = (int)((n_snap[0] + chunk_len - 1) / chunk_len);
+        const long long unit = (snap_tile + 31LL) / 32 * 32, S = n_snap[0];
+        cut.push_back(0);
+        while ((int)cut.size() < kMaxOutChunks && S - cut.back() >= kOutChunkMin) {
+            const long long len = ((S - cut.back()) / 2 + unit - 1) / unit * unit;
+            if (S - cut.back() - len < kOutChunkMin / 2) break;
+            cut.push_back(cut.back() + len);
+        }
+        cut.push_back(S);
+        n_out = (int)cut.size() - 1;
     }
     if (n_out > 1 && (r = ensure(c, S_DESC, sizeof(SceneDesc) * (1 + n_out)))) return r;
     if ((r = ensure(c, S_OUT, sizeof(uint32_t) * host_tab))) return r;
@@ -860,7 +868,7 @@ extern "C" int ivm_build_table(ivm_ctx *c, const ivm_scene *scenes, int32_t n_sc
     } else if (n_out > 1) {
         return table_in_chunks(c, g, scenes, hd, cfg, tx[0], rx[0], tx_off[0] >= 0,
                                rx_off[0] >= 0, table[0], los[0], tab_host[0], los_host[0],
-                               snap_tile, chunk_len, n_out, stats);
+                               snap_tile, cut, n_out, stats);
     } else {
         if ((r = enqueue(hd.data()))) return r;
     }

@@ -1,6 +1,8 @@
 """A table of one scene with the table or the LoS on the host is traversed in
 snapshot chunks, each chunk copied out on a second stream while the next is
-traversed.  The host rows must equal those of the same call with device
+traversed; each chunk is half of what is left, rounded up to the snapshot
+tile (itself rounded up to 32), while both parts keep at least 4,096
+snapshots.  The host rows must equal those of the same call with device
 outputs (one launch over every snapshot), and the rows on both sides of each
 chunk boundary must equal the oracle's."""
 import numpy as np
@@ -15,8 +17,19 @@ from tests.test_gpu_table_tiles import route
 pytestmark = pytest.mark.gpu
 
 FAST = ivm.IVM_FLAG_PERSISTENT | ivm.IVM_FLAG_OCCLUDER_CACHE | ivm.IVM_FLAG_DEDUP_SOURCES
-N_SNAP = 40077   # four chunks of 10,048 snapshots with tile 40, the last one ragged
-CHUNK = 10048
+N_SNAP = 40077   # tile 40: chunks of 20,096, 10,048, 4,992 and 4,941 snapshots
+
+
+def cuts(S, tile, least=8192, most=8):
+    """Chunk starts and the end, as the library lays them out."""
+    unit = (tile + 31) // 32 * 32
+    c = [0]
+    while len(c) < most and S - c[-1] >= least:
+        n = ((S - c[-1]) // 2 + unit - 1) // unit * unit
+        if S - c[-1] - n < least // 2:
+            break
+        c.append(c[-1] + n)
+    return c + [S]
 
 
 @pytest.fixture(scope="module")
@@ -52,10 +65,12 @@ def dev_out(W):
             torch.empty((N_SNAP,), dtype=torch.uint8, device="cuda:0"))
 
 
-def boundary_snaps():
+def boundary_snaps(tile=40):
+    c = cuts(N_SNAP, tile)
+    assert c == [0, 20096, 30144, 35136, N_SNAP] or tile != 40
     b = [0, 1, N_SNAP - 1]
-    for q in range(1, 4):
-        b += [q * CHUNK - 1, q * CHUNK]
+    for a in c[1:-1]:
+        b += [a - 1, a]
     return np.array(sorted(b))
 
 
@@ -107,13 +122,17 @@ def test_mixed_host_and_device_outputs(ctx, scene):
 @pytest.mark.parametrize("tile", [7, 2048])
 def test_chunk_length_follows_the_tile(ctx, scene, tile):
     """An odd tile (chunks rounded up to 32 snapshots) and a tile of 2,048
-    snapshots (chunks of five whole tiles) give the same rows as one launch."""
+    snapshots (chunks of whole tiles) give the same rows as one launch, and the
+    oracle's rows on both sides of every chunk boundary."""
     sc, rx, tx, _ = scene
     W = ivm.words(sc.n_facets)
     kw = dict(mode=ivm.IVM_MODE_FILTERED, flags=FAST, tile=tile)
     (T0, L0), _ = ivm.ivm_build_table(ctx, sc.facets, 3, tx, rx, out=dev_out(W), **kw)
     (T, L), _ = ivm.ivm_build_table(ctx, sc.facets, 3, tx, rx, out=host_out(W), **kw)
     assert (to_np(T) == to_np(T0)).all() and (L.numpy() == L0.cpu().numpy()).all()
+    snaps = boundary_snaps(tile)
+    tab, los = oracle.table(sc.facets, 3, tx, rx, snaps=snaps)
+    assert (to_np(T)[snaps] == tab).all() and (L.numpy()[snaps] == los).all()
 
 
 def test_error_in_a_later_chunk(ctx, scene):
@@ -126,7 +145,7 @@ def test_error_in_a_later_chunk(ctx, scene):
     (T0, L0), _ = ivm.ivm_build_table(ctx, sc.facets, 3, tx, rx, out=host_out(W), **kw)
     T0, L0 = to_np(T0).copy(), L0.numpy().copy()
     bad = rx.copy()
-    bad[2 * CHUNK + 17] = [1 << 21, 0, 150]   # 2^21 cm x 2s is beyond the coordinate range
+    bad[cuts(N_SNAP, 40)[2] + 17] = [1 << 21, 0, 150]   # 2^21 cm x 2s: beyond the range
     with pytest.raises(ivm.IvmError) as e:
         ivm.ivm_build_table(ctx, sc.facets, 3, tx, bad, out=host_out(W), **kw)
     assert e.value.code == ivm.IVM_ERR_RANGE
